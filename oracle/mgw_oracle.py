@@ -1,0 +1,402 @@
+"""Plain FP64 CPU oracle for the moment-conserving GW hot path.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product package imports, links or
+runs this module; only tests/, __graft_entry__.smoke() and the CPU-baseline
+leg of bench.py use it.  It shares no code with the CUDA library: both sides
+receive their inputs from mgw_inputs (which holds none of the method's
+arithmetic) and nothing else.
+
+It follows the paper (Backhouse, Allen, Scott, Booth, arXiv:2504.17439) step
+by step, in its order and notation, with numpy as the only helper (matrix
+products, eigh, solve).  The readings taken where the paper is silent or
+garbled are listed in the docstrings that use them:
+
+  R1  Eqs. 6-7 print W^(n) inside the sum over t; the Lehmann expansion
+      (eps_k - Omega)^n = sum_t C(n,t) eps_k^(n-t) (-Omega)^t needs the t-th
+      screened moment, so W^(t) is used.
+  R2  Spin: for restricted orbitals the singlet pole residues carry sqrt(2),
+      so Sigma(n) = 2 * sum ... with W(t) = eta~(t) V^T as in Eq. 15
+      (the same factor 2 that Eqs. 21-22 put into A and B).
+  R3  nmom_max = N means moments 0..2N+1 are built and conserved and the
+      block tridiagonal has N+1 diagonal blocks.
+  R4  Quadrature for Eqs. 24-25: Clenshaw-Curtis on x in [-1, 1] with nq+1
+      points, mapped to z = a (1+x)/(1-x), a = sqrt(D_min D_max); the x = 1
+      node (z = inf, integrand 0) is dropped, leaving nq nodes.  Both
+      integrals use the same nodes.
+  R5  Block Lanczos normalisation: symmetric (PSD) square roots for Sigma(0)
+      and every beta, so the blocks are unique; inverse square roots drop
+      eigenvalues below rank_tol * lambda_max.  Moments are centred by
+      c = tr Sigma(1) / tr Sigma(0) and scaled by
+      s = (tr M(2N) / tr M(0))^(1/2N) before the recursion (exact in
+      exact arithmetic; undone on the returned blocks).
+  R6  QP energy (Eq. 34): lowest alpha among the maximum weights.
+  R7  Aufbau (Eq. 40, Sec. III E): m minimising |N(m) - N_elec| over the
+      sorted poles, ties to the smaller m, mu = (E_{m-1} + E_m) / 2.
+  R8  Sigma_inf = 0 for a canonical Hartree-Fock reference (Eq. 8).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+# ----------------------------------------------------------------------------
+# Mean-field quantities
+
+
+def energy_differences(eps: np.ndarray, nocc: int) -> np.ndarray:
+    """D_{ia} = eps_a - eps_i, index ia = i*nvir + a (Eq. 20)."""
+    return (eps[None, nocc:] - eps[:nocc, None]).ravel()
+
+
+def particle_hole_block(L: np.ndarray, nocc: int) -> np.ndarray:
+    """V_{Q,ia}: the occupied-virtual slice of the DF tensor (Algorithm 1)."""
+    naux = L.shape[0]
+    return np.ascontiguousarray(L[:, :nocc, nocc:]).reshape(naux, -1)
+
+
+# ----------------------------------------------------------------------------
+# Density-response moments eta~(n) and W(n) = eta~(n) V^T
+
+
+def tda_response_moments(Lov: np.ndarray, D: np.ndarray, nmom: int) -> np.ndarray:
+    """TDA screening, Sec. II C.
+
+    eta~(0) = V (Eq. 32); eta~(n) = eta~(n-1) (D + 2 V^T V) (Eq. 33), applied
+    as eta~ D + 2 (eta~ V^T) V, the O(N_aux^2 ov) association the section
+    states.  Returns W(n) = eta~(n) V^T, the aux-basis factor of Eq. 15, for
+    n = 0..nmom-1 (no spin factor; see R2).
+    """
+    naux = Lov.shape[0]
+    W = np.empty((nmom, naux, naux))
+    T = Lov.copy()
+    for n in range(nmom):
+        W[n] = T @ Lov.T
+        if n + 1 < nmom:
+            T = T * D[None, :] + 2.0 * (W[n] @ Lov)
+    return W
+
+
+def clenshaw_curtis(n: int):
+    """Clenshaw-Curtis nodes x_k = cos(k pi / n), k = 0..n, and weights on
+    [-1, 1] (n even), from the closed cosine-sum form of the weights."""
+    assert n % 2 == 0 and n >= 2
+    k = np.arange(n + 1)
+    x = np.cos(k * math.pi / n)
+    w = np.empty(n + 1)
+    for kk in range(n + 1):
+        c = 1.0 if kk in (0, n) else 2.0
+        s = 0.0
+        for j in range(1, n // 2 + 1):
+            b = 1.0 if j == n // 2 else 2.0
+            s += b / (4.0 * j * j - 1.0) * math.cos(2.0 * j * kk * math.pi / n)
+        w[kk] = c / n * (1.0 - s)
+    return x, w
+
+
+def quadrature_rule(nq: int, dmin: float, dmax: float):
+    """Nodes z_j and weights w_j with  int_0^inf f(z) dz ~ sum_j w_j f(z_j)
+    (reading R4 of the quadrature the paper defers to its ref. for Eq. 24)."""
+    x, wx = clenshaw_curtis(nq)
+    x, wx = x[1:], wx[1:]  # drop x = 1 (z = infinity)
+    a = math.sqrt(dmin * dmax)
+    z = a * (1.0 + x) / (1.0 - x)
+    w = wx * 2.0 * a / (1.0 - x) ** 2
+    return z, w
+
+
+def rpa_eta0(Lov: np.ndarray, D: np.ndarray, nq: int) -> np.ndarray:
+    """RPA zeroth moment, Sec. II B, Eqs. 23-28.
+
+    G = G_main + G_offset with
+      G_main  = 1/pi int_{-inf}^{inf} z^2 Q(z) ((I + Q(z))^-1 - I) V F(z) dz
+      G_offset = V D + 4 int_0^inf V D E(z) V^T V E(z) dz
+      Q(z) = 4 V F(z) D V^T,  F(z) = (D^2 + z^2)^-1,  E(z) = exp(-z D),
+    the G_main integrand being even in z (so 1/pi over R = 2/pi over
+    [0, inf)), both by the rule of quadrature_rule; then
+      eta~(0) = G D^-1 (I - 4 V^T (I + 4 V D^-1 V^T)^-1 V D^-1).
+    """
+    naux = Lov.shape[0]
+    eye = np.eye(naux)
+    z, w = quadrature_rule(nq, float(D.min()), float(D.max()))
+    G_main = np.zeros_like(Lov)
+    G_off = Lov * D[None, :]
+    for zj, wj in zip(z, w):
+        F = 1.0 / (D * D + zj * zj)
+        Q = 4.0 * (Lov * (F * D)[None, :]) @ Lov.T
+        G_main += (2.0 / math.pi) * wj * zj * zj * ((Q @ (np.linalg.inv(eye + Q) - eye)) @ (Lov * F[None, :]))
+        E = np.exp(-zj * D)
+        G_off += 4.0 * wj * (((Lov * (D * E)[None, :]) @ Lov.T) @ (Lov * E[None, :]))
+    G = G_main + G_off
+    GDi = G / D[None, :]
+    S = eye + 4.0 * (Lov / D[None, :]) @ Lov.T
+    return GDi - 4.0 * (GDi @ Lov.T) @ np.linalg.solve(S, Lov / D[None, :])
+
+
+def rpa_response_moments(Lov: np.ndarray, D: np.ndarray, nmom: int, nq: int) -> np.ndarray:
+    """RPA screening, Sec. II B: eta~(0) from Eq. 23, eta~(1) = V D (Eq. 29),
+    eta~(n) = eta~(n-2) (D^2 + 4 V^T V D) (Eq. 30), applied as
+    eta~ D^2 + 4 (eta~ V^T)(V D).  Returns W(n) = eta~(n) V^T."""
+    naux = Lov.shape[0]
+    W = np.empty((nmom, naux, naux))
+    T = [rpa_eta0(Lov, D, nq), Lov * D[None, :]]
+    LD = Lov * D[None, :]
+    for n in range(nmom):
+        if n >= 2:
+            T.append(T[n - 2] * (D * D)[None, :] + 4.0 * (W[n - 2] @ LD))
+        W[n] = T[n] @ Lov.T
+    return W
+
+
+def response_moments(Lov, D, nmom, screening="tda", nq=48):
+    if screening == "tda":
+        return tda_response_moments(Lov, D, nmom)
+    if screening == "rpa":
+        return rpa_response_moments(Lov, D, nmom, nq)
+    raise ValueError(screening)
+
+
+# ----------------------------------------------------------------------------
+# Self-energy moments (Eqs. 6-7 with Eq. 15)
+
+
+def sigma_moments(eps: np.ndarray, nocc: int, L: np.ndarray, W: np.ndarray, rows=None):
+    """Hole and particle self-energy moments, Eqs. 6-7 (readings R1, R2).
+
+    For every Green's-function index x the screened moment
+    W^(t)_{px,qx} = sum_PQ V_{P,px} W(t)_{PQ} V_{Q,qx} (Eq. 15) is formed,
+    then Sigma(n,<)_pq = 2 sum_t C(n,t) (-1)^t sum_k eps_k^(n-t) W^(t)_{pk,qk}
+    and Sigma(n,>)_pq = 2 sum_t C(n,t) sum_c eps_c^(n-t) W^(t)_{pc,qc}.
+    `rows` restricts p to a subset (the full q range is returned).
+    """
+    nmom, naux = W.shape[0], W.shape[1]
+    nmo = eps.size
+    p_idx = np.arange(nmo) if rows is None else np.asarray(rows)
+    sh = np.zeros((nmom, p_idx.size, nmo))
+    sp = np.zeros((nmom, p_idx.size, nmo))
+    for x in range(nmo):
+        Lx = L[:, :, x]  # V_{P, p x} as [P][p]
+        Lxp = Lx[:, p_idx]
+        Wx = np.stack([Lxp.T @ W[t] @ Lx for t in range(nmom)])  # W^(t)_{px,qx}
+        hole = x < nocc
+        out = sh if hole else sp
+        sign = -1.0 if hole else 1.0
+        for n in range(nmom):
+            for t in range(n + 1):
+                out[n] += 2.0 * math.comb(n, t) * sign**t * eps[x] ** (n - t) * Wx[t]
+    return sh, sp
+
+
+# ----------------------------------------------------------------------------
+# Block Lanczos from moments (the upfolded effective Hamiltonian of Eq. 9)
+
+
+def _psd_sqrt(S, rank_tol):
+    """Symmetric square root and pseudo-inverse square root of a symmetric
+    PSD matrix, dropping eigenvalues below rank_tol * lambda_max."""
+    lam, U = np.linalg.eigh(0.5 * (S + S.T))
+    lmax = max(lam.max(), 0.0) if lam.size else 0.0
+    keep = lam > rank_tol * lmax if lmax > 0 else np.zeros_like(lam, dtype=bool)
+    r = int(keep.sum())
+    lk, Uk = lam[keep], U[:, keep]
+    sq = (Uk * np.sqrt(lk)) @ Uk.T
+    isq = (Uk / np.sqrt(lk)) @ Uk.T
+    return sq, isq, r, Uk, lk
+
+
+def block_lanczos(sig: np.ndarray, nblk: int, rank_tol: float = 1e-12):
+    """Block tridiagonal representation of one sector of the self-energy.
+
+    Given Sigma(n), n = 0..2 nblk - 1, return the coupling S0^(1/2),
+    diagonal blocks alpha_0..alpha_{nblk-1} and off-diagonal blocks
+    beta_1..beta_{nblk-1} of T with Sigma(n) = S0^(1/2) (T^n)_{00} S0^(1/2)
+    (the moment-conserving upfolding of Eqs. 9-10; block Lanczos three-term
+    recurrence run on inner products that are moments, reading R5).
+
+    The Lanczos vectors are kept as coefficient lists Q_i = sum_k H^k Q_0
+    C_{i,k}, so <Q_i, H^m Q_j> = sum_kl C_{i,k}^T S^(k+l+m) C_{j,l}.
+    Returns (coup, alpha[nblk], beta[nblk-1], rank); blocks are nmo x nmo
+    when Sigma(0) is full rank, rank x rank otherwise.
+    """
+    nmom, nmo = sig.shape[0], sig.shape[1]
+    assert nmom >= 2 * nblk
+    sig = 0.5 * (sig + np.transpose(sig, (0, 2, 1)))
+    # centre and scale (R5)
+    tr0 = np.trace(sig[0])
+    c = np.trace(sig[1]) / tr0 if tr0 > 0 else 0.0
+    M = np.zeros_like(sig[: 2 * nblk])
+    for n in range(2 * nblk):
+        for k in range(n + 1):
+            M[n] += math.comb(n, k) * (-c) ** (n - k) * sig[k]
+    top = 2 * nblk - 2
+    s = 1.0
+    if top > 0 and tr0 > 0 and np.trace(M[top]) > 0:
+        s = (np.trace(M[top]) / np.trace(M[0])) ** (1.0 / top)
+    sq0, _, r, Ur, lr = _psd_sqrt(M[0], rank_tol)
+    if r == 0:  # no coupling at all: an empty chain
+        return np.zeros((nmo, 0)), np.zeros((nblk, 0, 0)), np.zeros((nblk - 1, 0, 0)), 0
+    full = r == nmo
+    P = Ur / np.sqrt(lr)[None, :]  # nmo x r
+    Sh = np.stack([P.T @ (M[n] / s**n) @ P for n in range(2 * nblk)])  # r x r
+
+    def inner(X, Y, m):
+        acc = np.zeros((r, r))
+        for k, Xk in enumerate(X):
+            for l, Yl in enumerate(Y):
+                acc += Xk.T @ Sh[k + l + m] @ Yl
+        return acc
+
+    eye = np.eye(r)
+    C = [[eye]]
+    alpha, beta = [], []
+    for i in range(nblk):
+        a = inner(C[i], C[i], 1)
+        a = 0.5 * (a + a.T)
+        alpha.append(a)
+        if i == nblk - 1:
+            break
+        R = []
+        for k in range(i + 2):
+            Rk = np.zeros((r, r))
+            if k >= 1:
+                Rk += C[i][k - 1]
+            if k <= i:
+                Rk -= C[i][k] @ a
+            if i >= 1 and k <= i - 1:
+                Rk -= C[i - 1][k] @ beta[i - 1].T
+            R.append(Rk)
+        RR = inner(R, R, 0)
+        b, binv, _, _, _ = _psd_sqrt(RR, rank_tol)
+        beta.append(b)
+        C.append([Rk @ binv for Rk in R])
+    alpha = [s * a + c * eye for a in alpha]
+    beta = [s * b for b in beta]
+    if full:
+        # rotate every block from the eigenbasis of Sigma(0) to the orbital basis
+        U = Ur
+        alpha = [U @ a @ U.T for a in alpha]
+        beta = [U @ b @ U.T for b in beta]
+        coup = sq0
+    else:
+        coup = Ur * np.sqrt(lr)[None, :]
+    return coup, np.array(alpha), np.array(beta).reshape(-1, r, r), r
+
+
+# ----------------------------------------------------------------------------
+# Upfolded Hamiltonian, QP energies, Aufbau
+
+
+def upfolded_hamiltonian(fock, hole, part, zeta: float = 0.0):
+    """H~ of Eq. 9: [[f + Sigma_inf, W~], [W~^T, d~ + zeta]] with
+    W~ = [coup_h, 0, .., coup_p, 0, ..] and d~ = blockdiag(T_h, T_p), each T
+    block tridiagonal (alpha on the diagonal, beta below, beta^T above).
+    Block order: physical | hole chain | particle chain."""
+    nmo = fock.shape[0]
+    blocks = []
+    for coup, alpha, beta in (hole, part):
+        r = alpha.shape[1]
+        blocks.append((coup, alpha, beta, r))
+    dim = nmo + sum(b[1].shape[0] * b[3] for b in blocks)
+    H = np.zeros((dim, dim))
+    H[:nmo, :nmo] = fock
+    off = nmo
+    for coup, alpha, beta, r in blocks:
+        nb = alpha.shape[0]
+        H[:nmo, off : off + r] = coup
+        H[off : off + r, :nmo] = coup.T
+        for i in range(nb):
+            o = off + i * r
+            H[o : o + r, o : o + r] = alpha[i] + zeta * np.eye(r)
+            if i + 1 < nb:
+                H[o + r : o + 2 * r, o : o + r] = beta[i]
+                H[o : o + r, o + r : o + 2 * r] = beta[i].T
+        off += nb * r
+    return H
+
+
+def qp_energies(E: np.ndarray, chi_phys: np.ndarray) -> np.ndarray:
+    """Eq. 34: eps_p^QP = E_alpha, alpha = argmax_beta |chi_{p beta}|^2
+    (ties to the lowest alpha, R6)."""
+    return E[np.argmax(chi_phys**2, axis=1)]
+
+
+def aufbau(E: np.ndarray, weight: np.ndarray, nelec: float):
+    """Aufbau filling (Eq. 40, Sec. III E, reading R7).  E ascending.
+    Returns (m, mu, N(m)) with N(m) = 2 sum_{alpha < m} weight_alpha."""
+    Ncum = np.concatenate([[0.0], 2.0 * np.cumsum(weight)])
+    err = np.abs(Ncum - nelec)
+    m = int(np.argmin(err))
+    if m == 0:
+        mu = E[0] - 1.0
+    elif m == E.size:
+        mu = E[-1] + 1.0
+    else:
+        mu = 0.5 * (E[m - 1] + E[m])
+    return m, mu, Ncum[m]
+
+
+def qp_solve(fock, hole, part, nelec: float, zeta: float = 0.0):
+    """Diagonalise H~ (Eq. 9), form G's poles (Eq. 11), QP energies (Eq. 34)
+    and the Aufbau chemical potential and density (Eq. 40)."""
+    nmo = fock.shape[0]
+    H = upfolded_hamiltonian(fock, hole, part, zeta)
+    E, X = np.linalg.eigh(H)
+    chi = X[:nmo]
+    weight = np.sum(chi**2, axis=0)
+    eqp = qp_energies(E, chi)
+    m, mu, n_out = aufbau(E, weight, nelec)
+    rho = 2.0 * chi[:, :m] @ chi[:, :m].T
+    return dict(E=E, chi=chi, weight=weight, eps_qp=eqp, mu=mu, nelec=n_out, m=m, rho=rho)
+
+
+# ----------------------------------------------------------------------------
+# Drivers
+
+
+def g0w0(eps, L, nocc, nmom_max, screening="tda", nq=48, eps_w=None, rank_tol=1e-12, fock=None):
+    """One-shot G0W0, Algorithm 1 (Sigma_inf = 0, f = diag(eps), R8).
+    eps is eps^G; eps_w (default eps) defines D for the screening; fock
+    (default diag(eps)) is the physical block of H~."""
+    nmo = eps.size
+    nmom = 2 * nmom_max + 2
+    nblk = nmom_max + 1
+    epsw = eps if eps_w is None else eps_w
+    D = energy_differences(epsw, nocc)
+    Lov = particle_hole_block(L, nocc)
+    W = response_moments(Lov, D, nmom, screening, nq)
+    sh, sp = sigma_moments(eps, nocc, L, W)
+    hole = block_lanczos(sh, nblk, rank_tol)
+    part = block_lanczos(sp, nblk, rank_tol)
+    f = np.diag(eps) if fock is None else fock
+    qp = qp_solve(f, hole[:3], part[:3], 2.0 * nocc)
+    return dict(W=W, sigma_hole=sh, sigma_part=sp, hole=hole, part=part, **qp)
+
+
+def evgw(eps, L, nocc, nmom_max, screening="tda", nq=48, g0=False, w0=False,
+         conv_e=5.0 * 3.6749322e-5, max_iter=50):
+    """Eigenvalue self-consistency, Algorithm 3 / Sec. III B: eps^G and/or
+    eps^W are replaced by the QP energies of Eq. 34 until they change by less
+    than conv_e (5 meV by default) between iterations."""
+    epsG = eps.copy()
+    epsW = eps.copy()
+    f = np.diag(eps)
+    hist = []
+    for it in range(max_iter):
+        nmom = 2 * nmom_max + 2
+        D = energy_differences(epsW, nocc)
+        W = response_moments(particle_hole_block(L, nocc), D, nmom, screening, nq)
+        sh, sp = sigma_moments(epsG, nocc, L, W)
+        hole = block_lanczos(sh, nmom_max + 1)
+        part = block_lanczos(sp, nmom_max + 1)
+        qp = qp_solve(f, hole[:3], part[:3], 2.0 * nocc)
+        e_new = qp["eps_qp"]
+        dG = np.abs(e_new - epsG).max() if not g0 else 0.0
+        dW = np.abs(e_new - epsW).max() if not w0 else 0.0
+        hist.append(max(dG, dW))
+        if not g0:
+            epsG = e_new.copy()
+        if not w0:
+            epsW = e_new.copy()
+        if max(dG, dW) < conv_e:
+            return dict(eps_qp=e_new, iterations=it + 1, converged=True, history=hist)
+    return dict(eps_qp=e_new, iterations=max_iter, converged=False, history=hist)

@@ -1,0 +1,128 @@
+"""Plant plausible mistakes in a copy of the oracle and check a pin catches each.
+
+Each case rewrites one line of an oracle function's source (a dropped term,
+a wrong sign or factor, the garbled W^(n) index of Eqs. 6-7, a transposed
+operand), executes the mutant in a namespace of its own and runs the same
+brute-force comparison the pins use.  The mutant must fail it.  The real
+oracle module is never modified.
+"""
+import inspect
+import math
+import types
+
+import numpy as np
+import pytest
+
+import brute
+import mgw_inputs
+from oracle import mgw_oracle as orc
+
+
+def mutant(func_names, old, new):
+    """A copy of the oracle module with `old` replaced by `new` inside one of
+    the named functions (exactly one occurrence), executed whole in a fresh
+    namespace so every function of the copy calls the mutated one."""
+    full = inspect.getsource(orc)
+    hit = 0
+    for name in func_names:
+        src = inspect.getsource(getattr(orc, name))
+        if old in src:
+            hit += src.count(old)
+            assert full.count(src) == 1
+            full = full.replace(src, src.replace(old, new))
+    assert hit == 1, (old, hit)
+    mod = types.ModuleType("oracle_mutant")
+    exec(compile(full, "<oracle mutant>", "exec"), mod.__dict__)
+    return mod
+
+
+def system(nocc=3, nvir=5, naux=12, seed=7, scale=2.0):
+    eps = mgw_inputs.orbital_energies(nocc, nvir, seed)
+    return eps, mgw_inputs.df_tensor(naux, nocc + nvir, seed) * scale
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def sigma_pin_error(mod, screening="tda"):
+    eps, L = system()
+    nmom = 8
+    D = mod.energy_differences(eps, 3)
+    W = mod.response_moments(mod.particle_hole_block(L, 3), D, nmom, screening, 48)
+    sh, sp = mod.sigma_moments(eps, 3, L, W)
+    bh, bp = brute.sigma_lehmann(eps, L, 3, nmom, screening)
+    return max(max(rel(sh[n], bh[n]), rel(sp[n], bp[n])) for n in range(nmom))
+
+
+def lanczos_pin_error(mod):
+    eps, L = system(nocc=3, nvir=6, naux=14)
+    nmom = 8
+    W = orc.tda_response_moments(orc.particle_hole_block(L, 3), orc.energy_differences(eps, 3), nmom)
+    sh, _ = orc.sigma_moments(eps, 3, L, W)
+    coup, alpha, beta, r = mod.block_lanczos(sh, 4)
+    T = brute.block_tridiagonal(alpha, beta)
+    err, Tn = 0.0, np.eye(T.shape[0])
+    for n in range(nmom):
+        err = max(err, rel(coup @ Tn[:r, :r] @ coup.T, sh[n]))
+        Tn = Tn @ T
+    return err
+
+
+def qp_pin_error(mod):
+    eps, L = system()
+    r = orc.g0w0(eps, L, 3, 2)
+    H = mod.upfolded_hamiltonian(np.diag(eps), r["hole"][:3], r["part"][:3])
+    nmo = eps.size
+    Wt, dt = H[:nmo, nmo:], H[nmo:, nmo:]
+    err, Dn = 0.0, np.eye(dt.shape[0])
+    for n in range(6):
+        err = max(err, rel(Wt @ Dn @ Wt.T, r["sigma_hole"][n] + r["sigma_part"][n]))
+        Dn = Dn @ dt
+    return err
+
+
+CASES = [
+    # (functions, old, new, pin, screening)
+    (["tda_response_moments"], "T * D[None, :] + 2.0 *", "T * D[None, :] + 1.0 *", "sigma", "tda"),
+    (["tda_response_moments"], "T * D[None, :] + 2.0 * (W[n] @ Lov)", "2.0 * (W[n] @ Lov)", "sigma", "tda"),
+    (["tda_response_moments"], "W[n] = T @ Lov.T", "W[n] = Lov @ T.T @ np.eye(Lov.shape[0]) * 0 + T @ T.T", "sigma", "tda"),
+    (["rpa_response_moments"], "(D * D)[None, :] + 4.0", "(D * D)[None, :] + 2.0", "sigma", "rpa"),
+    (["rpa_response_moments"], "Lov * D[None, :]]", "Lov]", "sigma", "rpa"),
+    (["rpa_eta0"], "G_off += 4.0 * wj", "G_off += 2.0 * wj", "sigma", "rpa"),
+    (["rpa_eta0"], "(np.linalg.inv(eye + Q) - eye)", "(np.linalg.inv(eye + Q) + eye)", "sigma", "rpa"),
+    (["rpa_eta0"], "S = eye + 4.0 *", "S = eye - 4.0 *", "sigma", "rpa"),
+    (["sigma_moments"], "sign = -1.0 if hole else 1.0", "sign = 1.0", "sigma", "tda"),
+    (["sigma_moments"], "out[n] += 2.0 *", "out[n] += 1.0 *", "sigma", "tda"),
+    (["sigma_moments"], "eps[x] ** (n - t) * Wx[t]", "eps[x] ** (n - t) * Wx[n]", "sigma", "tda"),
+    (["sigma_moments"], "math.comb(n, t)", "1", "sigma", "tda"),
+    (["sigma_moments"], "Lxp.T @ W[t] @ Lx", "Lxp.T @ W[t] @ Lx * (1 + 0.01)", "sigma", "tda"),
+    (["block_lanczos"], "Rk -= C[i][k] @ a", "Rk -= a @ C[i][k] * 0.5", "lanczos", None),
+    (["block_lanczos"], "Rk -= C[i - 1][k] @ beta[i - 1].T", "Rk -= C[i - 1][k] @ beta[i - 1].T * 0.0", "lanczos", None),
+    (["block_lanczos"], "acc += Xk.T @ Sh[k + l + m] @ Yl", "acc += Xk.T @ Sh[k + l] @ Yl", "lanczos", None),
+    (["block_lanczos"], "alpha = [s * a + c * eye for a in alpha]", "alpha = [s * a for a in alpha]", "lanczos", None),
+    (["upfolded_hamiltonian"], "H[o + r : o + 2 * r, o : o + r] = beta[i]", "H[o + r : o + 2 * r, o : o + r] = 0.5 * beta[i]", "qp", None),
+    (["upfolded_hamiltonian"], "H[:nmo, off : off + r] = coup", "H[:nmo, off : off + r] = coup.T @ coup", "qp", None),
+]
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_pins_catch_planted_mistake(case):
+    funcs, old, new, pin, screening = CASES[case]
+    mod = mutant(funcs, old, new)
+    if pin == "sigma":
+        err = sigma_pin_error(mod, screening)
+    elif pin == "lanczos":
+        err = lanczos_pin_error(mod)
+    else:
+        err = qp_pin_error(mod)
+    assert not (err < 1e-6), f"planted mistake went unnoticed: {old!r} -> {new!r} (err {err})"
+
+
+def test_unmutated_copy_passes_every_pin():
+    mod = mutant(["sigma_moments"], "out[n] += 2.0 *", "out[n] += 2.0 *")
+    assert sigma_pin_error(mod, "tda") < 1e-10
+    assert sigma_pin_error(mod, "rpa") < 1e-9
+    assert lanczos_pin_error(mod) < 1e-9
+    assert qp_pin_error(mod) < 1e-9
+    assert math.isfinite(lanczos_pin_error(orc))
