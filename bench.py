@@ -1,0 +1,339 @@
+#!/usr/bin/env python
+"""Benchmark of the moment-conserving GW self-energy moment build on GB300.
+
+A step is one pass of the hot path over one synthetic molecule-sized system
+(nocc 60, nvir 340, naux 1600, nmom_max 7, TDA, FP64): particle-hole block,
+response moments W(t), hole/particle Sigma(n) moments, block Lanczos of both
+sectors, and the upfolded-Hamiltonian QP solve.
+
+Metric: seconds per Sigma-moment build (response + Sigma moments, inputs
+resident in HBM), lower is better.  The JSON line also carries the full step
+time, an end-to-end number through the C ABI with host buffers (H2D of eps
+and L, D2H of both Sigma tensors inside the timed region), the roofline of
+the dominant kernel measured live with CUDA events, the CPU oracle timed on
+a bounded sample of the same workload, and SM clocks sampled during the run.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mgw|reference]
+
+Multi-GPU (torchrun): every rank runs an independent replica of the whole
+step (the path is not sharded here); value = max-over-ranks timed seconds /
+total builds, scaling "weak".
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import mgw_inputs  # noqa: E402
+
+WORKLOAD = "g0w0-nmo400-naux1600"
+METRIC = "sigma_moment_build_s"
+FP64_PEAK_GFLOPS = 1250.0  # nominal GB300 FP64 (DFMA) rate; the ALU bound of the FP64 path
+
+
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def work_flops(shape):
+    """Algorithmic flops of one Sigma-moment build (TDA): response (two GEMMs
+    per order, none after the last update) + Y stage + GEMM2."""
+    nmom, naux, nmo, ov = shape.nmom, shape.naux, shape.nmo, shape.ov
+    resp = 2.0 * naux * naux * ov * nmom + 2.0 * naux * naux * ov * (nmom - 1)
+    y = 2.0 * nmom * naux * naux * nmo * nmo
+    g2 = 2.0 * nmom * naux * nmo * nmo * nmo
+    return resp, y, g2
+
+
+# ---------------------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+        sm = [num(r[0]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower() == "active"})
+        loaded = [s for s in sm if s == s]
+        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": num(rows[0][1]),
+                "power_w_max": max(num(r[2]) for r in rows), "samples": len(rows), "reasons": reasons}
+
+
+# ---------------------------------------------------------------------------- CPU oracle
+
+
+def oracle_sample(shape, eps, L, resp_rows=160, sig_rows=(4, 12)):
+    """Time the CPU oracle on a bounded sample of the workload and scale it to
+    one full Sigma-moment build: the TDA response for `resp_rows` of naux aux
+    rows (rows are independent, cost linear in rows), and Sigma moments for
+    two small sets of orbital rows p (a + b * rows fit, evaluated at nmo)."""
+    from oracle import mgw_oracle as orc
+
+    nocc = shape.nocc
+    D = orc.energy_differences(eps, nocc)
+    Lov = orc.particle_hole_block(L, nocc)
+    rows = np.linspace(0, shape.naux - 1, resp_rows).astype(int)
+    t0 = time.perf_counter()
+    Wr = orc.tda_response_moments(Lov, D, shape.nmom, rows=rows)
+    t_resp = (time.perf_counter() - t0) * shape.naux / resp_rows
+    # a full-shape W for the Sigma timing (values do not change the cost)
+    W = np.zeros((shape.nmom, shape.naux, shape.naux))
+    W[:, rows, :] = Wr
+    ts = []
+    for r in sig_rows:
+        t0 = time.perf_counter()
+        orc.sigma_moments(eps, nocc, L, W, rows=list(range(r)))
+        ts.append(time.perf_counter() - t0)
+    b = (ts[1] - ts[0]) / (sig_rows[1] - sig_rows[0])
+    a = ts[0] - b * sig_rows[0]
+    t_sig = a + b * shape.nmo
+    cores = os.cpu_count()
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
+        if os.environ.get(var, "").isdigit():
+            cores = int(os.environ[var])
+    sample = (f"TDA response for {resp_rows}/{shape.naux} aux rows (x{shape.naux / resp_rows:.0f}) + Sigma moments "
+              f"for {sig_rows[0]} and {sig_rows[1]} of {shape.nmo} orbital rows (linear fit to {shape.nmo})")
+    return t_resp + t_sig, cores, sample
+
+
+# ---------------------------------------------------------------------------- reference arm
+
+
+def run_reference(args):
+    rank = env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    shape, seed = mgw_inputs.workload(args.workload)
+    eps, L = mgw_inputs.system(shape, seed)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, cores, sample = oracle_sample(shape, eps, L)
+        if i >= args.warmup:
+            vals.append(v)
+    value = statistics.mean(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "nocc": shape.nocc, "nvir": shape.nvir, "naux": shape.naux,
+                   "nmom_max": shape.nmom_max, "screening": "tda"},
+        "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------- GPU arm
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2504_17439_gb300 import build, driver, mgw
+
+    rank, world, local = env_int("RANK", 0), env_int("WORLD_SIZE", 1), env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    shape, seed = mgw_inputs.workload(args.workload)
+    eps_np, L_np = mgw_inputs.system(shape, seed)
+    nocc, nvir, naux, nmo, nmom = shape.nocc, shape.nvir, shape.naux, shape.nmo, shape.nmom
+    nblk = shape.nmom_max + 1
+    eps_h = torch.from_numpy(eps_np).pin_memory()
+    L_h = torch.from_numpy(L_np).pin_memory()
+    eps = eps_h.cuda()
+    L = L_h.cuda()
+    stream = torch.cuda.current_stream()
+    h = mgw.Handle(local, stream)
+    o = mgw.options(screening=mgw.MGW_TDA if args.screening == "tda" else mgw.MGW_RPA)
+    Lov = torch.empty((naux, nocc * nvir), dtype=torch.float64, device="cuda")
+    W = torch.empty((nmom, naux, naux), dtype=torch.float64, device="cuda")
+    sh = torch.empty((nmom, nmo, nmo), dtype=torch.float64, device="cuda")
+    sp = torch.empty_like(sh)
+    fock = torch.diag(eps).contiguous()
+
+    def step():
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        h.mgw_extract_ov(nocc, nvir, L, Lov)
+        h.mgw_response_moments(o, nocc, nvir, naux, nmom, eps, Lov, W)
+        h.mgw_sigma_moments(o, nocc, nvir, naux, nmom, eps, L, W, sh, sp)
+        ev[1].record(stream)
+        ch, ah, bh, rh = h.mgw_block_lanczos(o, nmo, nmom, sh)
+        cp, ap, bp, rp = h.mgw_block_lanczos(o, nmo, nmom, sp)
+        qp = h.mgw_qp_solve(o, nmo, nblk, rh, rp, fock, (ch, ah, bh), (cp, ap, bp), 0.0, 2.0 * nocc)
+        ev[2].record(stream)
+        return ev, qp
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    launches0 = h.launches
+    h.profile(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    t_wall = time.perf_counter()
+    recs = [step()[0] for _ in range(args.steps)]
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    launches = h.launches - launches0
+    build_s = [a.elapsed_time(b) / 1e3 for a, b, _ in recs]
+    step_s = [a.elapsed_time(c) / 1e3 for a, _, c in recs]
+    ny, ty_ms = h.profile_query("sigma_y_binomial")
+    n2, t2_ms = h.profile_query("sigma_gemm2")
+    nw, tw_ms = h.profile_query("w_gemm")
+    nt, tt_ms = h.profile_query("t_update")
+    h.profile(False)
+    resp_f, y_f, g2_f = work_flops(shape)
+    # per launch of the dominant kernel: its share of the Y-stage flops
+    y_per_launch = y_f * args.steps / max(ny, 1)
+    y_avg_s = ty_ms / 1e3 / max(ny, 1)
+    achieved = y_per_launch / y_avg_s / 1e9 if ny else None
+
+    # end to end through the C ABI with host buffers
+    sh_h = torch.empty(sh.shape, dtype=torch.float64).pin_memory()
+    sp_h = torch.empty(sp.shape, dtype=torch.float64).pin_memory()
+    e2e = []
+    for i in range(args.warmup + args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        eps.copy_(eps_h, non_blocking=True)
+        L.copy_(L_h, non_blocking=True)
+        h.mgw_extract_ov(nocc, nvir, L, Lov)
+        h.mgw_response_moments(o, nocc, nvir, naux, nmom, eps, Lov, W)
+        h.mgw_sigma_moments(o, nocc, nvir, naux, nmom, eps, L, W, sh, sp)
+        sh_h.copy_(sh, non_blocking=True)
+        sp_h.copy_(sp, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        if i >= args.warmup:
+            e2e.append(a.elapsed_time(b) / 1e3)
+
+    def ranks_max(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    total_build = ranks_max(sum(build_s))
+    total_step = ranks_max(sum(step_s))
+    total_e2e = ranks_max(sum(e2e))
+    builds = args.steps * world
+    value = total_build / builds
+    line = None
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_step / builds * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "nocc": nocc, "nvir": nvir, "naux": naux,
+                       "nmom_max": shape.nmom_max, "screening": args.screening, "precision": "fp64",
+                       "l2": "inputs larger than L2 (L is %.2f GB)" % (L.numel() * 8 / 1e9)},
+            "stages_s": {"sigma_build": statistics.mean(build_s), "full_step": statistics.mean(step_s),
+                         "w_gemm": tw_ms / 1e3 / args.steps, "t_update": tt_ms / 1e3 / args.steps,
+                         "sigma_y_binomial": ty_ms / 1e3 / args.steps, "sigma_gemm2": t2_ms / 1e3 / args.steps},
+            "gflops_sigma_build": (resp_f + y_f + g2_f) / statistics.mean(build_s) / 1e9,
+            "roofline": {"kernel": "sigma_y_binomial", "bound": "alu", "achieved": achieved,
+                         "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                         "frac": achieved / FP64_PEAK_GFLOPS if achieved else None, "traffic": None,
+                         "peak_source": "nominal FP64 rate (profiling recipe table), of fallback"},
+            "e2e": {"value": total_e2e / builds, "unit": "s",
+                    "h2d_bytes_per_step": int(L_h.numel() * 8 + eps_h.numel() * 8),
+                    "d2h_bytes_per_step": int(2 * sh.numel() * 8)},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "wall_s": t_wall,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            v, cores, sample = oracle_sample(shape, eps_np, L_np)
+            line["cpu_baseline"] = {"value": v, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    h.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mgw", choices=["mgw", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(mgw_inputs.WORKLOADS))
+    ap.add_argument("--screening", default="tda", choices=["tda", "rpa"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

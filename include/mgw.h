@@ -1,0 +1,196 @@
+/*
+ * mgw.h -- C ABI of libmgw: the density-fitted construction of moment-
+ * conserving GW self-energy moments on one GB300 (sm_103a), after
+ * Backhouse, Allen, Scott & Booth, arXiv:2504.17439.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Array arguments are DEVICE pointers to row-major float64 data owned by
+ *    the caller, unless a parameter says "host".  They must stay valid until
+ *    the work queued on the handle's stream has completed.
+ *  - Calls are stream ordered on the stream given to mgw_create (or
+ *    mgw_set_stream).  Arguments are checked before anything is queued.
+ *    Calls whose outputs include host scalars synchronise the stream.
+ *  - The library owns its workspace (device memory inside the handle).  It
+ *    grows to the largest size a call has needed and is released by
+ *    mgw_destroy.  A handle is used by one host thread at a time.
+ *  - Index conventions: orbitals are ordered occupied first (ascending
+ *    energy) then virtual; particle-hole pairs ia are ordered i-major,
+ *    a fastest (ia = i*nvir + a); moments are indexed n = 0..nmom-1.
+ *  - Nothing throws across the ABI.  A failing call returns a negative
+ *    mgw_status and mgw_last_error() describes it.  Numerical failures
+ *    (a non positive definite matrix, a broken-down recurrence) are reported
+ *    as statuses, never as a device fault.
+ *
+ * Notation of the paper: V_{P,ia} is the particle-hole block of the DF
+ * tensor (here Lov), eta~(n) the aux-basis response moment, D_ia the
+ * orbital-energy differences, Sigma(n,<)/(n,>) the hole/particle moments.
+ */
+#ifndef MGW_H
+#define MGW_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MGW_OK = 0,
+  MGW_ERR_ARG = -1,         /* bad size, null pointer, NaN in an input scalar */
+  MGW_ERR_CUDA = -2,        /* a CUDA runtime or library call failed */
+  MGW_ERR_NOMEM = -3,       /* workspace allocation failed */
+  MGW_ERR_NOT_PD = -4,      /* a matrix required positive definite was not */
+  MGW_ERR_BREAKDOWN = -5,   /* block Lanczos lost rank it could not handle */
+  MGW_ERR_NO_CONV = -6,     /* an iteration hit its cap before converging */
+  MGW_ERR_TIMEOUT = -7,     /* a bounded device wait gave up */
+  MGW_ERR_UNSUPPORTED = -8  /* option or size outside what is built */
+} mgw_status;
+
+typedef enum { MGW_TDA = 0, MGW_RPA = 1 } mgw_screening;
+
+/* Arithmetic of the bulk contractions.  FP64: float64 throughout. */
+typedef enum { MGW_FP64 = 0, MGW_BF16X3 = 1 } mgw_precision;
+
+typedef struct mgw_handle mgw_handle;
+
+typedef struct {
+  int screening;     /* mgw_screening; default MGW_TDA */
+  int precision;     /* mgw_precision; default MGW_FP64 */
+  int nquad;         /* quadrature nodes for the RPA eta~(0) (Eqs. 24-25); default 48, even, >= 2 */
+  int xchunk;        /* Green's-function indices x per pass of the Sigma build; 0 = automatic */
+  double rank_tol;   /* relative eigenvalue cut for inverse square roots; default 1e-12 */
+  int max_iter;      /* iteration cap of self-consistent loops; default 50 */
+  double conv_e;     /* energy threshold, Ha; default 5 meV = 1.8375e-4 Ha (Sec. IV B) */
+  double conv_mom;   /* max |delta Sigma(n)| threshold; default 1e-4 (Sec. IV B) */
+  int diis_space;    /* DIIS vectors kept in the Fock loop; default 12 (Sec. IV B) */
+} mgw_options;
+
+/* Fill *o with the defaults listed above. */
+void mgw_options_default(mgw_options* o);
+
+/* Create a handle on CUDA device `device`, queueing on `cuda_stream`
+ * (a cudaStream_t, or NULL for the default stream). */
+mgw_status mgw_create(mgw_handle** h, int device, void* cuda_stream);
+mgw_status mgw_destroy(mgw_handle* h);
+mgw_status mgw_set_stream(mgw_handle* h, void* cuda_stream);
+/* Text of the last error on this handle ("" if none).  Owned by the handle. */
+const char* mgw_last_error(const mgw_handle* h);
+/* Bytes of device workspace the handle currently holds. */
+size_t mgw_workspace_bytes(const mgw_handle* h);
+
+/*
+ * Tracing.  mgw_profile(h, 1) clears the record and starts timing every
+ * GEMM-class kernel the handle launches with a pair of CUDA events on its
+ * stream; mgw_profile(h, 0) stops (both synchronise).  mgw_profile_query
+ * sums the recorded launches whose kernel name equals `name` ("*" for all):
+ * names are "w_gemm", "t_update", "sigma_y_binomial", "sigma_gemm2",
+ * "gemm_nn", "gemm_nt", "gemm_tn".  mgw_launch_count returns the number of
+ * kernels of this library the handle has launched since creation (solver
+ * library kernels are not counted).
+ */
+mgw_status mgw_profile(mgw_handle* h, int enable);
+mgw_status mgw_profile_query(mgw_handle* h, const char* name, long* count, double* total_ms);
+long mgw_launch_count(const mgw_handle* h);
+
+/*
+ * mgw_extract_ov -- V_{Q,ia} = L[Q][i][nocc + a]: copy the particle-hole
+ * block of the DF tensor into its own array (the first of the two
+ * transformed copies of Algorithm 1).
+ *   L   [naux][nmo][nmo]   in
+ *   Lov [naux][nocc*nvir]  out
+ */
+mgw_status mgw_extract_ov(mgw_handle* h, int nocc, int nvir, int naux,
+                          const double* L, double* Lov);
+
+/*
+ * mgw_response_moments -- W(n) = eta~(n) V^T for n = 0..nmom-1.
+ * TDA (Sec. II C, Eqs. 32-33): eta~(0) = V, eta~(n) = eta~(n-1)(D + 2 V^T V).
+ * RPA (Sec. II B, Eqs. 23-30): eta~(0) by the quadrature of Eqs. 24-28 with
+ *   o->nquad nodes, eta~(1) = V D, eta~(n) = eta~(n-2)(D^2 + 4 V^T V D).
+ * D_ia = eps_W[nocc+a] - eps_W[i] (Eq. 20); W(n) is the naux x naux inner
+ * factor of Eq. 15 (no spin factor).
+ *   eps_W [nmo]                 in   orbital energies defining D
+ *   Lov   [naux][nocc*nvir]     in   V
+ *   Wmom  [nmom][naux][naux]    out  symmetric
+ * Requires nocc, nvir, naux >= 1, 1 <= nmom <= 64, D_ia > 0 for RPA.
+ */
+mgw_status mgw_response_moments(mgw_handle* h, const mgw_options* o,
+                                int nocc, int nvir, int naux, int nmom,
+                                const double* eps_W, const double* Lov,
+                                double* Wmom);
+
+/*
+ * mgw_sigma_moments -- hole and particle self-energy moments, Eqs. 6-7 with
+ * Eq. 15, with the t-th screened moment inside the sum over t and the
+ * restricted spin factor 2:
+ *   Sigma(n,<)_pq = 2 sum_t C(n,t) (-1)^t sum_k eps_k^(n-t) [L_k^T W(t) L_k]_pq
+ *   Sigma(n,>)_pq = 2 sum_t C(n,t)        sum_c eps_c^(n-t) [L_c^T W(t) L_c]_pq
+ * where (L_x)_{P,p} = L[P][p][x].
+ *   eps_G    [nmo]               in   Green's-function energies
+ *   L        [naux][nmo][nmo]    in   symmetric in its last two indices
+ *   Wmom     [nmom][naux][naux]  in   from mgw_response_moments
+ *   sig_hole [nmom][nmo][nmo]    out
+ *   sig_part [nmom][nmo][nmo]    out
+ * Requires 1 <= nmom <= 24.
+ */
+mgw_status mgw_sigma_moments(mgw_handle* h, const mgw_options* o,
+                             int nocc, int nvir, int naux, int nmom,
+                             const double* eps_G, const double* L,
+                             const double* Wmom,
+                             double* sig_hole, double* sig_part);
+
+/*
+ * mgw_block_lanczos -- moment-conserving upfolding of one sector (Eqs. 9-10):
+ * coupling S0^(1/2), diagonal blocks alpha_0..alpha_{nblk-1} and
+ * off-diagonal blocks beta_1..beta_{nblk-1} of a block tridiagonal T with
+ *   Sigma(n) = S0^(1/2) (T^n)_{00} S0^(1/2),  n = 0..2 nblk - 1,
+ * nblk = nmom / 2.  Symmetric positive square roots are used for S0 and for
+ * every beta, so the blocks are unique.  Moments are centred on
+ * c = tr Sigma(1)/tr Sigma(0) and scaled by s = (tr M(2nblk-2)/tr M(0))^(1/(2nblk-2))
+ * inside (exact in exact arithmetic).  Eigenvalues below
+ * o->rank_tol * lambda_max of Sigma(0) are dropped; the retained rank r is
+ * returned and, when r < nmo, the blocks are r x r in the leading corner of
+ * each nmo x nmo slot (basis: retained eigenvectors of Sigma(0)).
+ *   sig   [nmom][nmo][nmo]        in   one sector, symmetric
+ *   coup  [nmo][nmo]              out
+ *   alpha [nblk][nmo][nmo]        out
+ *   beta  [nblk-1][nmo][nmo]      out  (may be NULL when nblk == 1)
+ *   rank  host int                out  (synchronises)
+ * Requires nmom even, 2 <= nmom <= 24.
+ */
+mgw_status mgw_block_lanczos(mgw_handle* h, const mgw_options* o,
+                             int nmo, int nmom, const double* sig,
+                             double* coup, double* alpha, double* beta,
+                             int* rank);
+
+/*
+ * mgw_qp_solve -- diagonalise the upfolded Hamiltonian of Eq. 9
+ *   H~ = [[fock, W~], [W~^T, d~ + zeta]],  W~ = [coup_h 0 .. | coup_p 0 ..],
+ *   d~ = blockdiag(T_h, T_p),
+ * block order physical | hole chain | particle chain, dim = nmo + nblk (r_h + r_p).
+ * Then the QP energies of Eq. 34 (argmax of |chi_{p alpha}|^2, ties to the
+ * lowest alpha), the Aufbau filling of Eq. 40 (m minimising |N(m) - nelec|,
+ * ties to the smaller m, mu = (E_{m-1} + E_m)/2) and the correlated density
+ * rho = 2 sum_{alpha < m} chi chi^T.
+ *   fock [nmo][nmo]; coup_*, alpha_*, beta_* as written by mgw_block_lanczos
+ *   (leading r x r of each nmo x nmo slot is used)              in
+ *   E [dim] ascending, weight [dim] = sum_p chi_{p alpha}^2      out
+ *   chi_phys [nmo][dim] (or NULL), eps_qp [nmo], rho [nmo][nmo] (or NULL)  out
+ *   mu_host, nelec_host, m_host: host scalars (may be NULL)      out (synchronises)
+ */
+mgw_status mgw_qp_solve(mgw_handle* h, const mgw_options* o,
+                        int nmo, int nblk, int rank_h, int rank_p,
+                        const double* fock,
+                        const double* coup_h, const double* alpha_h, const double* beta_h,
+                        const double* coup_p, const double* alpha_p, const double* beta_p,
+                        double zeta, double nelec,
+                        double* E, double* weight, double* chi_phys,
+                        double* eps_qp, double* rho,
+                        double* mu_host, double* nelec_host, int* m_host);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MGW_H */

@@ -59,17 +59,18 @@ def particle_hole_block(L: np.ndarray, nocc: int) -> np.ndarray:
 # Density-response moments eta~(n) and W(n) = eta~(n) V^T
 
 
-def tda_response_moments(Lov: np.ndarray, D: np.ndarray, nmom: int) -> np.ndarray:
+def tda_response_moments(Lov: np.ndarray, D: np.ndarray, nmom: int, rows=None) -> np.ndarray:
     """TDA screening, Sec. II C.
 
     eta~(0) = V (Eq. 32); eta~(n) = eta~(n-1) (D + 2 V^T V) (Eq. 33), applied
     as eta~ D + 2 (eta~ V^T) V, the O(N_aux^2 ov) association the section
     states.  Returns W(n) = eta~(n) V^T, the aux-basis factor of Eq. 15, for
-    n = 0..nmom-1 (no spin factor; see R2).
+    n = 0..nmom-1 (no spin factor; see R2).  Row P of eta~(n) = V A^n
+    depends on row P of V alone, so `rows` restricts P to a subset and
+    returns W(n)[rows, :].
     """
-    naux = Lov.shape[0]
-    W = np.empty((nmom, naux, naux))
-    T = Lov.copy()
+    T = Lov.copy() if rows is None else Lov[np.asarray(rows)].copy()
+    W = np.empty((nmom, T.shape[0], Lov.shape[0]))
     for n in range(nmom):
         W[n] = T @ Lov.T
         if n + 1 < nmom:
@@ -164,26 +165,26 @@ def sigma_moments(eps: np.ndarray, nocc: int, L: np.ndarray, W: np.ndarray, rows
     """Hole and particle self-energy moments, Eqs. 6-7 (readings R1, R2).
 
     For every Green's-function index x the screened moment
-    W^(t)_{px,qx} = sum_PQ V_{P,px} W(t)_{PQ} V_{Q,qx} (Eq. 15) is formed,
-    then Sigma(n,<)_pq = 2 sum_t C(n,t) (-1)^t sum_k eps_k^(n-t) W^(t)_{pk,qk}
-    and Sigma(n,>)_pq = 2 sum_t C(n,t) sum_c eps_c^(n-t) W^(t)_{pc,qc}.
+    W^(t)_{px,qx} = sum_PQ V_{P,px} W(t)_{PQ} V_{Q,qx} (Eq. 15) is formed
+    (all x at once, one matrix product per x), then
+      Sigma(n,<)_pq = 2 sum_t C(n,t) (-1)^t sum_k eps_k^(n-t) W^(t)_{pk,qk}
+      Sigma(n,>)_pq = 2 sum_t C(n,t)        sum_c eps_c^(n-t) W^(t)_{pc,qc}.
     `rows` restricts p to a subset (the full q range is returned).
     """
-    nmom, naux = W.shape[0], W.shape[1]
+    nmom = W.shape[0]
     nmo = eps.size
     p_idx = np.arange(nmo) if rows is None else np.asarray(rows)
+    Lx = np.ascontiguousarray(L.transpose(2, 0, 1))  # [x][Q][q] = V_{Q,qx}
+    Lxp = np.ascontiguousarray(Lx[:, :, p_idx].transpose(0, 2, 1))  # [x][p][P] = V_{P,px}
     sh = np.zeros((nmom, p_idx.size, nmo))
     sp = np.zeros((nmom, p_idx.size, nmo))
-    for x in range(nmo):
-        Lx = L[:, :, x]  # V_{P, p x} as [P][p]
-        Lxp = Lx[:, p_idx]
-        Wx = np.stack([Lxp.T @ W[t] @ Lx for t in range(nmom)])  # W^(t)_{px,qx}
-        hole = x < nocc
-        out = sh if hole else sp
-        sign = -1.0 if hole else 1.0
-        for n in range(nmom):
-            for t in range(n + 1):
-                out[n] += 2.0 * math.comb(n, t) * sign**t * eps[x] ** (n - t) * Wx[t]
+    for t in range(nmom):
+        Wx = (Lxp @ W[t]) @ Lx  # [x][p][q] = W^(t)_{px,qx}
+        for hole, xs, out in ((True, slice(0, nocc), sh), (False, slice(nocc, nmo), sp)):
+            sign = -1.0 if hole else 1.0
+            for n in range(t, nmom):
+                wgt = 2.0 * math.comb(n, t) * sign**t * eps[xs] ** (n - t)
+                out[n] += np.tensordot(wgt, Wx[xs], axes=1)
     return sh, sp
 
 

@@ -1,0 +1,299 @@
+// Internal declarations of libmgw: the handle, workspace, error plumbing and
+// the FP64 tiled GEMM template every FP64 contraction of the library uses.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cusolverDn.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "mgw.h"
+
+struct mgw_handle {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cusolverDnHandle_t solver = nullptr;
+  void* ws = nullptr;        // device workspace, grows to the high-water mark
+  size_t ws_bytes = 0;
+  int* dinfo = nullptr;      // device int for solver status words
+  std::string err;
+  // tracing: launches counted always; CUDA-event pairs per GEMM launch when enabled
+  long launches = 0;
+  bool prof = false;
+  struct Span { const char* name; cudaEvent_t a, b; };
+  std::vector<Span> spans;
+};
+
+namespace mgw {
+
+mgw_status fail(mgw_handle* h, mgw_status s, const char* fmt, ...);
+
+#define MGW_CUDA(h, call)                                                          \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      return mgw::fail((h), MGW_ERR_CUDA, "%s failed: %s (%s:%d)", #call,           \
+                       cudaGetErrorString(e_), __FILE__, __LINE__);                \
+  } while (0)
+
+#define MGW_SOLVER(h, call)                                                        \
+  do {                                                                             \
+    cusolverStatus_t s_ = (call);                                                  \
+    if (s_ != CUSOLVER_STATUS_SUCCESS)                                             \
+      return mgw::fail((h), MGW_ERR_CUDA, "%s failed: cusolver status %d (%s:%d)", \
+                       #call, (int)s_, __FILE__, __LINE__);                        \
+  } while (0)
+
+#define MGW_TRY(expr)                 \
+  do {                                \
+    mgw_status st_ = (expr);          \
+    if (st_ != MGW_OK) return st_;    \
+  } while (0)
+
+// Ensure the handle's workspace holds at least `bytes`; grows (never shrinks).
+mgw_status ws_reserve(mgw_handle* h, size_t bytes);
+
+// Bump allocator over the handle's workspace for the duration of one call.
+struct Arena {
+  size_t need = 0;
+  std::vector<std::pair<double**, size_t>> slots;
+  void add(double** p, size_t count) {
+    slots.push_back({p, count});
+    need += ((count * sizeof(double) + 255) / 256) * 256;
+  }
+  mgw_status commit(mgw_handle* h) {
+    mgw_status s = ws_reserve(h, need);
+    if (s != MGW_OK) return s;
+    char* base = static_cast<char*>(h->ws);
+    size_t off = 0;
+    for (auto& sl : slots) {
+      *sl.first = reinterpret_cast<double*>(base + off);
+      off += ((sl.second * sizeof(double) + 255) / 256) * 256;
+    }
+    return MGW_OK;
+  }
+};
+
+inline mgw_status check_launch(mgw_handle* h, const char* what) {
+  ++h->launches;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    return fail(h, MGW_ERR_CUDA, "launch of %s failed: %s", what, cudaGetErrorString(e));
+  return MGW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 GEMM  C(m, n) (op)= sum_k A(m, k) B(k, n)
+// 256 threads as a 16 x 16 grid, each owning a (BM/16) x (BN/16) block of
+// C in a strided pattern (rows ty + 16 i, columns tx + 16 j), K stepped by 16
+// with a double-buffered shared-memory stage fed from registers.  FP64 FMA is
+// the bound on this part, so the tile only has to keep the DFMA pipe busy.
+//
+// Operand accessors give the address of element (m, k) of A / (k, n) of B
+// for one batch entry; `kContig` says which index is contiguous in memory so
+// the tile loads coalesce along it.
+
+struct ARowMajor {  // A(m,k) = p[m*ld + k]
+  const double* p; long ld; long bstride;
+  static constexpr bool kContig = true;
+  __device__ const double* base(int b) const { return p + (long)b * bstride; }
+  __device__ long off(long m, long k) const { return m * ld + k; }
+  __device__ bool ok(long, long) const { return true; }
+};
+struct AKMajor2 {  // A(m,k) = p[(k/kdiv)*kshi + (k%kdiv)*kslo + m]
+  const double* p; long kdiv, kshi, kslo; long bstride;
+  static constexpr bool kContig = false;
+  __device__ const double* base(int b) const { return p + (long)b * bstride; }
+  __device__ long off(long m, long k) const { return (k / kdiv) * kshi + (k % kdiv) * kslo + m; }
+  __device__ bool ok(long, long) const { return true; }
+};
+// Rows of the stacked moments W[t][P][:] in groups of PB aux rows with all
+// nmom orders of a group adjacent; a group occupies gsz >= nmom*PB rows:
+// m = g*gsz + t*PB + pl, P = g*PB + pl (rows past nmom*PB are padding).
+struct AGroupedMoments {
+  const double* p; int nmom, PB, naux, gsz;
+  static constexpr bool kContig = true;
+  __device__ const double* base(int) const { return p; }
+  __device__ bool split(long m, int& t, int& P) const {
+    long g = m / gsz; int r = (int)(m % gsz);
+    t = r / PB; P = (int)g * PB + r % PB;
+    return r < nmom * PB && P < naux;
+  }
+  __device__ long off(long m, long k) const {
+    int t, P; split(m, t, P);
+    return ((long)t * naux + P) * naux + k;
+  }
+  __device__ bool ok(long m, long) const { int t, P; return split(m, t, P); }
+};
+struct BRowMajor {  // B(k,n) = p[k*ld + n]
+  const double* p; long ld; long bstride;
+  static constexpr bool kContig = false;
+  __device__ const double* base(int b) const { return p + (long)b * bstride; }
+  __device__ long off(long k, long n) const { return k * ld + n; }
+};
+struct BNMajor {  // B(k,n) = p[n*ld + k]
+  const double* p; long ld; long bstride;
+  static constexpr bool kContig = true;
+  __device__ const double* base(int b) const { return p + (long)b * bstride; }
+  __device__ long off(long k, long n) const { return n * ld + k; }
+};
+
+// Epilogues: called once per owned element after the K loop.
+struct EpiStore {  // C = alpha*acc + beta*C
+  double* c; long ldc; long bstride; double alpha, beta;
+  __device__ void operator()(int b, long m, long n, double acc) const {
+    double* q = c + (long)b * bstride + m * ldc + n;
+    *q = beta == 0.0 ? alpha * acc : alpha * acc + beta * *q;
+  }
+};
+struct EpiDiagUpdate {  // C = C * d[n] + alpha*acc   (the D-plus-low-rank update)
+  double* c; long ldc; const double* d; double alpha;
+  __device__ void operator()(int, long m, long n, double acc) const {
+    double* q = c + m * ldc + n;
+    *q = *q * d[n] + alpha * acc;
+  }
+};
+
+template <class Epi, class = void>
+struct is_tile_epi { static constexpr bool value = false; };
+template <class Epi>
+struct is_tile_epi<Epi, decltype(void(Epi::kTile))> { static constexpr bool value = Epi::kTile; };
+
+template <int BM, int BN, class AOp, class BOp, class Epi>
+__global__ void __launch_bounds__(256)
+dgemm_kernel(long M, long N, long K, AOp A, BOp B, Epi epi) {
+  constexpr int BK = 16, TM = BM / 16, TN = BN / 16;
+  constexpr int LA = BM * BK / 256, LB = BN * BK / 256;
+  constexpr int SA = BK * (BM + 1), SB = BK * (BN + 1);
+  // [As0 | As1 | Bs0 | Bs1]; reused by tile epilogues after the K loop
+  __shared__ double smem[2 * SA + 2 * SB];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const long m0 = (long)blockIdx.y * BM, n0 = (long)blockIdx.x * BN;
+  const int bz = blockIdx.z;
+  const double* Ab = A.base(bz);
+  const double* Bb = B.base(bz);
+  double acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
+  double ra[LA], rb[LB];
+
+  auto gload = [&](long k0) {
+#pragma unroll
+    for (int e = 0; e < LA; ++e) {
+      int idx = tid + e * 256, mm, kk;
+      if (AOp::kContig) { mm = idx / BK; kk = idx % BK; } else { kk = idx / BM; mm = idx % BM; }
+      long m = m0 + mm, k = k0 + kk;
+      ra[e] = (m < M && k < K && A.ok(m, k)) ? __ldg(Ab + A.off(m, k)) : 0.0;
+    }
+#pragma unroll
+    for (int e = 0; e < LB; ++e) {
+      int idx = tid + e * 256, nn, kk;
+      if (BOp::kContig) { nn = idx / BK; kk = idx % BK; } else { kk = idx / BN; nn = idx % BN; }
+      long n = n0 + nn, k = k0 + kk;
+      rb[e] = (n < N && k < K) ? __ldg(Bb + B.off(k, n)) : 0.0;
+    }
+  };
+  auto sstore = [&](int buf) {
+    double* As = smem + buf * SA;
+    double* Bs = smem + 2 * SA + buf * SB;
+#pragma unroll
+    for (int e = 0; e < LA; ++e) {
+      int idx = tid + e * 256, mm, kk;
+      if (AOp::kContig) { mm = idx / BK; kk = idx % BK; } else { kk = idx / BM; mm = idx % BM; }
+      As[kk * (BM + 1) + mm] = ra[e];
+    }
+#pragma unroll
+    for (int e = 0; e < LB; ++e) {
+      int idx = tid + e * 256, nn, kk;
+      if (BOp::kContig) { nn = idx / BK; kk = idx % BK; } else { kk = idx / BN; nn = idx % BN; }
+      Bs[kk * (BN + 1) + nn] = rb[e];
+    }
+  };
+
+  gload(0);
+  sstore(0);
+  __syncthreads();
+  int cur = 0;
+  for (long k0 = 0; k0 < K; k0 += BK) {
+    const bool more = k0 + BK < K;
+    if (more) gload(k0 + BK);
+    const double* As = smem + cur * SA;
+    const double* Bs = smem + 2 * SA + cur * SB;
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double a[TM], b[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[kk * (BM + 1) + ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk * (BN + 1) + tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    if (more) sstore(cur ^ 1);
+    __syncthreads();
+    cur ^= 1;
+  }
+  if constexpr (is_tile_epi<Epi>::value) {
+    epi.template tile<BM, BN, TM, TN>(bz, m0, n0, M, N, acc, smem, 2 * SA + 2 * SB);
+  } else {
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      long m = m0 + ty + 16 * i;
+      if (m >= M) continue;
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        long n = n0 + tx + 16 * j;
+        if (n < N) epi(bz, m, n, acc[i][j]);
+      }
+    }
+  }
+}
+
+template <int BM, int BN, class AOp, class BOp, class Epi>
+mgw_status dgemm(mgw_handle* h, long M, long N, long K, int batch, const AOp& A, const BOp& B,
+                 const Epi& epi, const char* what) {
+  if (M <= 0 || N <= 0 || batch <= 0) return MGW_OK;
+  dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM), (unsigned)batch);
+  cudaEvent_t ea = nullptr, eb = nullptr;
+  if (h->prof) {
+    cudaEventCreate(&ea);
+    cudaEventCreate(&eb);
+    cudaEventRecord(ea, h->stream);
+  }
+  dgemm_kernel<BM, BN, AOp, BOp, Epi><<<grid, 256, 0, h->stream>>>(M, N, K, A, B, epi);
+  mgw_status st = check_launch(h, what);
+  if (h->prof) {
+    cudaEventRecord(eb, h->stream);
+    h->spans.push_back({what, ea, eb});
+  }
+  return st;
+}
+
+// Plain row-major helpers: C = alpha * op(A) op(B) + beta * C (single matrix).
+mgw_status gemm_nn(mgw_handle* h, long M, long N, long K, double alpha, const double* A, long lda,
+                   const double* B, long ldb, double beta, double* C, long ldc);
+mgw_status gemm_nt(mgw_handle* h, long M, long N, long K, double alpha, const double* A, long lda,
+                   const double* B, long ldb, double beta, double* C, long ldc);
+mgw_status gemm_tn(mgw_handle* h, long M, long N, long K, double alpha, const double* A, long lda,
+                   const double* B, long ldb, double beta, double* C, long ldc);
+
+// Dense FP64 helpers built on the solver library (symmetric eigensolve,
+// Cholesky factor + solve).  Row-major symmetric matrices; on return of
+// syevd, row j of `a` holds eigenvector j (eigenvalues ascending in w).
+mgw_status syevd(mgw_handle* h, int n, double* a, double* w);
+mgw_status potrf_potrs(mgw_handle* h, int n, double* a, int nrhs, double* b, bool* not_pd);
+
+// Small elementwise kernels
+mgw_status energy_differences(mgw_handle* h, int nocc, int nvir, const double* eps, double* D);
+mgw_status scale_columns(mgw_handle* h, long rows, long cols, const double* src, const double* d,
+                         double* dst);  // dst[r][c] = src[r][c] * d[c]
+mgw_status add_identity(mgw_handle* h, int n, double* a, double s);  // a += s * I
+
+}  // namespace mgw

@@ -1,0 +1,225 @@
+// Density-response moments in the auxiliary basis, FP64 path.
+//
+// TDA (Sec. II C, Eqs. 32-33):  T(0) = V,  T(n+1) = T(n) o D + 2 W(n) V
+// RPA (Sec. II B, Eqs. 23-30):  T(0) = eta~(0) by quadrature,  T(1) = V o D,
+//                               T(n) = T(n-2) o D^2 + 4 W(n-2) (V o D)
+// with W(n) = T(n) V^T (the aux-basis factor of Eq. 15).  "o D" scales the
+// columns ia by D_ia.  Each order is two GEMMs: W(n) (naux x naux, K = ov)
+// and the update, whose epilogue applies the diagonal term in place, so T
+// is read and written once per order and no intermediate is stored.
+#include "mgw_internal.h"
+
+#include <cmath>
+#include <vector>
+
+namespace mgw {
+
+// W = T V^T : A = T [naux][ov] row-major, B(k=ia, n=Q) = V[Q][ia]
+static mgw_status w_gemm(mgw_handle* h, int naux, long ov, const double* T, const double* V, double* W) {
+  return dgemm<64, 64>(h, naux, naux, ov, 1, ARowMajor{T, ov, 0}, BNMajor{V, ov, 0},
+                       EpiStore{W, naux, 0, 1.0, 0.0}, "w_gemm");
+}
+
+// T = T o d + alpha * W B : A = W [naux][naux], B = [naux][ov] row-major
+static mgw_status t_update(mgw_handle* h, int naux, long ov, const double* W, const double* B,
+                           double* T, const double* d, double alpha) {
+  return dgemm<64, 64>(h, naux, ov, naux, 1, ARowMajor{W, naux, 0}, BRowMajor{B, ov, 0},
+                       EpiDiagUpdate{T, ov, d, alpha}, "t_update");
+}
+
+// ---------------------------------------------------------------------------
+// Quadrature for Eqs. 24-25: Clenshaw-Curtis on x in [-1, 1] with nq + 1
+// points (x_k = cos(k pi / nq)), mapped to z = a (1 + x)/(1 - x) with
+// a = sqrt(D_min D_max); the x = 1 node (z = infinity, where both
+// integrands vanish) is dropped.  Weights are the closed cosine-sum form of
+// the Clenshaw-Curtis weights times dz/dx = 2a/(1-x)^2.
+static void quadrature(int nq, double dmin, double dmax, std::vector<double>& z, std::vector<double>& w) {
+  const double pi = 3.14159265358979323846;
+  const double a = std::sqrt(dmin * dmax);
+  z.clear();
+  w.clear();
+  for (int k = 1; k <= nq; ++k) {
+    double x = std::cos(k * pi / nq);
+    double s = 0.0;
+    for (int j = 1; j <= nq / 2; ++j) {
+      double b = (j == nq / 2) ? 1.0 : 2.0;
+      s += b / (4.0 * j * j - 1.0) * std::cos(2.0 * j * k * pi / nq);
+    }
+    double c = (k == nq) ? 1.0 : 2.0;
+    double wx = c / nq * (1.0 - s);
+    z.push_back(a * (1.0 + x) / (1.0 - x));
+    w.push_back(wx * 2.0 * a / ((1.0 - x) * (1.0 - x)));
+  }
+}
+
+// elementwise column factors for one node: f = F D, F, D E, E
+__global__ void k_node_factors(long ov, const double* D, double z, double* fFD, double* fF, double* fDE,
+                               double* fE) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i >= ov) return;
+  double d = D[i];
+  double F = 1.0 / (d * d + z * z);
+  double E = exp(-z * d);
+  fFD[i] = F * d;
+  fF[i] = F;
+  fDE[i] = d * E;
+  fE[i] = E;
+}
+
+__global__ void k_sub_inplace(long n, double* x, const double* y) {  // x -= y
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i < n) x[i] -= y[i];
+}
+__global__ void k_recip_sq(long n, const double* D, double* r, double* d2) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i < n) { r[i] = 1.0 / D[i]; d2[i] = D[i] * D[i]; }
+}
+
+// eta~(0) of the RPA, Eqs. 23-28 (see the quadrature note above).
+static mgw_status rpa_eta0(mgw_handle* h, int naux, long ov, int nq, const double* V, const double* D,
+                           double dmin, double dmax, double* T0, double* work) {
+  // work layout: G[naux*ov] B1[naux*ov] Q[naux^2] X[naux^2] IQ[naux^2] fac[4*ov]
+  const long na2 = (long)naux * naux;
+  double* G = work;
+  double* B1 = G + naux * ov;
+  double* Q = B1 + naux * ov;
+  double* X = Q + na2;
+  double* IQ = X + na2;
+  double* fFD = IQ + na2;
+  double* fF = fFD + ov;
+  double* fDE = fF + ov;
+  double* fE = fDE + ov;
+  const double pi = 3.14159265358979323846;
+  std::vector<double> z, w;
+  quadrature(nq, dmin, dmax, z, w);
+  const unsigned gov = (unsigned)((ov + 255) / 256);
+
+  // G_offset starts at V D
+  MGW_TRY(scale_columns(h, naux, ov, V, D, G));
+  for (int j = 0; j < nq; ++j) {
+    k_node_factors<<<gov, 256, 0, h->stream>>>(ov, D, z[j], fFD, fF, fDE, fE);
+    MGW_TRY(check_launch(h, "node_factors"));
+    // Q = 4 V F D V^T  (Eq. 26)
+    MGW_TRY(scale_columns(h, naux, ov, V, fFD, B1));
+    MGW_TRY(gemm_nt(h, naux, naux, ov, 4.0, B1, ov, V, ov, 0.0, Q, naux));
+    // X = Q (I + Q)^-1 - Q  (= Q((I+Q)^-1 - I), Eq. 24; Q and (I+Q)^-1 commute)
+    MGW_CUDA(h, cudaMemcpyAsync(X, Q, sizeof(double) * na2, cudaMemcpyDeviceToDevice, h->stream));
+    MGW_CUDA(h, cudaMemcpyAsync(IQ, Q, sizeof(double) * na2, cudaMemcpyDeviceToDevice, h->stream));
+    MGW_TRY(add_identity(h, naux, IQ, 1.0));
+    bool not_pd = false;
+    MGW_TRY(potrf_potrs(h, naux, IQ, naux, X, &not_pd));
+    k_sub_inplace<<<(unsigned)((na2 + 255) / 256), 256, 0, h->stream>>>(na2, X, Q);
+    MGW_TRY(check_launch(h, "sub"));
+    // G += (2/pi) w z^2 X (V F)   (integrand even in z: 1/pi over R = 2/pi over [0, inf))
+    MGW_TRY(scale_columns(h, naux, ov, V, fF, B1));
+    MGW_TRY(gemm_nn(h, naux, ov, naux, (2.0 / pi) * w[j] * z[j] * z[j], X, naux, B1, ov, 1.0, G, ov));
+    // G += 4 w (V D E V^T)(V E)   (Eq. 25)
+    MGW_TRY(scale_columns(h, naux, ov, V, fDE, B1));
+    MGW_TRY(gemm_nt(h, naux, naux, ov, 1.0, B1, ov, V, ov, 0.0, Q, naux));
+    MGW_TRY(scale_columns(h, naux, ov, V, fE, B1));
+    MGW_TRY(gemm_nn(h, naux, ov, naux, 4.0 * w[j], Q, naux, B1, ov, 1.0, G, ov));
+  }
+  // eta~(0) = G D^-1 (I - 4 V^T (I + 4 V D^-1 V^T)^-1 V D^-1)   (Eq. 23)
+  double* rD = fFD;
+  double* d2 = fF;
+  k_recip_sq<<<gov, 256, 0, h->stream>>>(ov, D, rD, d2);
+  MGW_TRY(check_launch(h, "recip"));
+  MGW_TRY(scale_columns(h, naux, ov, G, rD, T0));  // T0 = G D^-1
+  MGW_TRY(scale_columns(h, naux, ov, V, rD, B1));  // B1 = V D^-1
+  MGW_TRY(gemm_nt(h, naux, naux, ov, 4.0, B1, ov, V, ov, 0.0, Q, naux));  // S - I
+  MGW_TRY(add_identity(h, naux, Q, 1.0));
+  MGW_TRY(gemm_nt(h, naux, naux, ov, 1.0, T0, ov, V, ov, 0.0, X, naux));  // Y = G D^-1 V^T
+  bool not_pd = false;
+  MGW_TRY(potrf_potrs(h, naux, Q, naux, X, &not_pd));                      // X = Y S^-1
+  MGW_TRY(gemm_nn(h, naux, ov, naux, -4.0, X, naux, B1, ov, 1.0, T0, ov));
+  return MGW_OK;
+}
+
+__global__ void k_minmax(long n, const double* D, double* out) {
+  // single block reduction of min and max
+  __shared__ double smin[256], smax[256];
+  double lo = 1e300, hi = -1e300;
+  for (long i = threadIdx.x; i < n; i += blockDim.x) { lo = fmin(lo, D[i]); hi = fmax(hi, D[i]); }
+  smin[threadIdx.x] = lo;
+  smax[threadIdx.x] = hi;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + s]);
+      smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + s]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { out[0] = smin[0]; out[1] = smax[0]; }
+}
+
+}  // namespace mgw
+
+using namespace mgw;
+
+extern "C" mgw_status mgw_response_moments(mgw_handle* h, const mgw_options* o, int nocc, int nvir, int naux,
+                                           int nmom, const double* eps_W, const double* Lov, double* Wmom) {
+  if (!h) return MGW_ERR_ARG;
+  mgw_options def;
+  mgw_options_default(&def);
+  if (!o) o = &def;
+  if (nocc < 1 || nvir < 1 || naux < 1 || nmom < 1 || nmom > 64 || !eps_W || !Lov || !Wmom)
+    return fail(h, MGW_ERR_ARG, "mgw_response_moments: bad sizes or null pointer");
+  if (o->screening != MGW_TDA && o->screening != MGW_RPA)
+    return fail(h, MGW_ERR_ARG, "mgw_response_moments: unknown screening %d", o->screening);
+  if (o->screening == MGW_RPA && (o->nquad < 2 || o->nquad % 2))
+    return fail(h, MGW_ERR_ARG, "mgw_response_moments: nquad must be even and >= 2");
+  if (o->precision != MGW_FP64)
+    return fail(h, MGW_ERR_UNSUPPORTED, "mgw_response_moments: precision %d not built", o->precision);
+  MGW_CUDA(h, cudaSetDevice(h->device));
+  const long ov = (long)nocc * nvir;
+  const long na2 = (long)naux * naux;
+  const long tsz = (long)naux * ov;
+
+  Arena ar;
+  double *D = nullptr, *T0 = nullptr, *T1 = nullptr, *aux = nullptr, *work = nullptr, *mm = nullptr;
+  ar.add(&D, ov);
+  ar.add(&T0, tsz);
+  ar.add(&mm, 2);
+  if (o->screening == MGW_RPA) {
+    ar.add(&T1, tsz);
+    ar.add(&aux, tsz + 2 * ov);  // V o D, D^2, spare
+    ar.add(&work, 2 * tsz + 3 * na2 + 4 * ov);
+  }
+  MGW_TRY(ar.commit(h));
+  MGW_TRY(energy_differences(h, nocc, nvir, eps_W, D));
+
+  if (o->screening == MGW_TDA) {
+    MGW_CUDA(h, cudaMemcpyAsync(T0, Lov, sizeof(double) * tsz, cudaMemcpyDeviceToDevice, h->stream));
+    for (int n = 0; n < nmom; ++n) {
+      double* Wn = Wmom + (long)n * na2;
+      MGW_TRY(w_gemm(h, naux, ov, T0, Lov, Wn));
+      if (n + 1 < nmom) MGW_TRY(t_update(h, naux, ov, Wn, Lov, T0, D, 2.0));
+    }
+    return MGW_OK;
+  }
+
+  // RPA
+  k_minmax<<<1, 256, 0, h->stream>>>(ov, D, mm);
+  MGW_TRY(check_launch(h, "minmax"));
+  double hmm[2];
+  MGW_CUDA(h, cudaMemcpyAsync(hmm, mm, sizeof hmm, cudaMemcpyDeviceToHost, h->stream));
+  MGW_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (!(hmm[0] > 0.0))
+    return fail(h, MGW_ERR_ARG, "mgw_response_moments: RPA needs D_ia > 0 (min D = %g)", hmm[0]);
+  double* LD = aux;
+  double* D2 = aux + tsz;
+  double* rD = D2 + ov;
+  k_recip_sq<<<(unsigned)((ov + 255) / 256), 256, 0, h->stream>>>(ov, D, rD, D2);
+  MGW_TRY(check_launch(h, "recip"));
+  MGW_TRY(scale_columns(h, naux, ov, Lov, D, LD));
+  MGW_TRY(rpa_eta0(h, naux, ov, o->nquad, Lov, D, hmm[0], hmm[1], T0, work));
+  MGW_CUDA(h, cudaMemcpyAsync(T1, LD, sizeof(double) * tsz, cudaMemcpyDeviceToDevice, h->stream));
+  double* T[2] = {T0, T1};
+  for (int n = 0; n < nmom; ++n) {
+    double* Wn = Wmom + (long)n * na2;
+    if (n >= 2) MGW_TRY(t_update(h, naux, ov, Wmom + (long)(n - 2) * na2, LD, T[n & 1], D2, 4.0));
+    MGW_TRY(w_gemm(h, naux, ov, T[n & 1], Lov, Wn));
+  }
+  return MGW_OK;
+}

@@ -1,0 +1,144 @@
+// Hole and particle self-energy moments, FP64 path (Eqs. 6-7 with Eq. 15).
+//
+//   Sigma(n)_pq = 2 sum_x sum_t C(n,t) s^t eps_x^(n-t) [L_x^T W(t) L_x]_pq,
+//   s = -1 for the hole sector (x occupied), +1 for the particle sector.
+//
+// Per chunk of Green's-function indices x (all in one sector):
+//  1. Y-stage GEMM with every moment order stacked along M:
+//       Y(t)[P][(x,q)] = sum_Q W(t)[P][Q] L[Q][x][q]       (L symmetric in x,q)
+//     Its M tile holds all nmom orders of a few aux rows P, so the epilogue
+//     applies the binomial weighting in shared memory and writes only
+//       Z(n)[P][(x,q)] = 2 sum_{t<=n} C(n,t) s^t eps_x^(n-t) Y(t)[P][(x,q)];
+//     Y never reaches HBM.
+//  2. GEMM2, batched over n:  Sigma(n)[p][q] += sum_{P,x} L[P][x][p] Z(n)[P][(x,q)].
+#include "mgw_internal.h"
+
+#include <algorithm>
+#include <cmath>
+
+namespace mgw {
+
+constexpr int kMaxMom = 24;
+
+struct BinomCoef {
+  double c[kMaxMom * (kMaxMom + 1) / 2];  // 2 C(n,t) s^t, row n at n(n+1)/2
+};
+
+// Tile epilogue of the Y stage: rows of the tile are (t, pl) with
+// t = r / PB, pl = r % PB; columns are (x_local, q) of the chunk.
+struct EpiBinomial {
+  static constexpr bool kTile = true;
+  double* Z;           // [nmom][naux][ncol]
+  const double* eps;   // eps_x of the chunk's first x at eps[0]
+  int nmom, PB, naux, nmo;
+  long ncol;           // xc * nmo
+  BinomCoef bc;
+
+  template <int BM, int BN, int TM, int TN>
+  __device__ void tile(int, long m0, long n0, long, long N, double (&acc)[TM][TN], double* smem,
+                       int smem_len) const {
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    constexpr int HALF = BN / 2;  // stage half the columns at a time
+    static_assert((TN % 2) == 0, "TN must be even");
+    const long g = m0 / BM;        // tile == one group of PB aux rows
+    (void)smem_len;
+    for (int hf = 0; hf < 2; ++hf) {
+      __syncthreads();
+      // acc columns tx + 16 j with j in [hf*TN/2, (hf+1)*TN/2) -> smem [BM][HALF+1]
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int jj = 0; jj < TN / 2; ++jj) {
+          int j = hf * (TN / 2) + jj;
+          int col = tx + 16 * j - hf * HALF;
+          smem[(ty + 16 * i) * (HALF + 1) + col] = acc[i][j];
+        }
+      __syncthreads();
+      const int pairs = PB * HALF;
+      for (int pi = tid; pi < pairs; pi += 256) {
+        int pl = pi / HALF, col = pi % HALF;
+        long P = g * PB + pl;
+        long n = n0 + hf * HALF + col;
+        if (P >= naux || n >= N) continue;
+        double e = eps[n / nmo];
+        double y[kMaxMom], pe[kMaxMom];
+        pe[0] = 1.0;
+        for (int t = 0; t < nmom; ++t) {
+          y[t] = smem[(t * PB + pl) * (HALF + 1) + col];
+          if (t + 1 < nmom) pe[t + 1] = pe[t] * e;
+        }
+        for (int nn = 0; nn < nmom; ++nn) {
+          const double* cr = bc.c + nn * (nn + 1) / 2;
+          double z = 0.0;
+          for (int t = 0; t <= nn; ++t) z = fma(cr[t] * pe[nn - t], y[t], z);
+          Z[((long)nn * naux + P) * ncol + n] = z;
+        }
+      }
+    }
+  }
+};
+
+}  // namespace mgw
+
+using namespace mgw;
+
+extern "C" mgw_status mgw_sigma_moments(mgw_handle* h, const mgw_options* o, int nocc, int nvir, int naux,
+                                        int nmom, const double* eps_G, const double* L, const double* Wmom,
+                                        double* sig_hole, double* sig_part) {
+  if (!h) return MGW_ERR_ARG;
+  mgw_options def;
+  mgw_options_default(&def);
+  if (!o) o = &def;
+  if (nocc < 1 || nvir < 1 || naux < 1 || nmom < 1 || nmom > kMaxMom || !eps_G || !L || !Wmom || !sig_hole ||
+      !sig_part)
+    return fail(h, MGW_ERR_ARG, "mgw_sigma_moments: bad sizes or null pointer");
+  if (o->precision != MGW_FP64)
+    return fail(h, MGW_ERR_UNSUPPORTED, "mgw_sigma_moments: precision %d not built", o->precision);
+  MGW_CUDA(h, cudaSetDevice(h->device));
+  const int nmo = nocc + nvir;
+  constexpr int BM = 96, BN = 64;
+  const int PB = std::max(1, BM / nmom);
+  const long ngroups = (naux + PB - 1) / PB;
+
+  // chunk of x per pass: Z holds nmom * naux * xc * nmo doubles (~1 GiB budget)
+  const double per_x = (double)nmom * naux * nmo * sizeof(double);
+  int xc = o->xchunk > 0 ? o->xchunk : (int)std::max(1.0, std::floor((1024.0 * 1024 * 1024) / per_x));
+  xc = std::min(xc, nmo);
+
+  Arena ar;
+  double* Z = nullptr;
+  ar.add(&Z, (size_t)nmom * naux * xc * nmo);
+  MGW_TRY(ar.commit(h));
+
+  for (int sector = 0; sector < 2; ++sector) {
+    const int xbeg = sector == 0 ? 0 : nocc, xend = sector == 0 ? nocc : nmo;
+    const double sgn = sector == 0 ? -1.0 : 1.0;
+    double* sig = sector == 0 ? sig_hole : sig_part;
+    BinomCoef bc;
+    for (int n = 0; n < nmom; ++n) {
+      double c = 1.0, s = 1.0;
+      for (int t = 0; t <= n; ++t) {
+        bc.c[n * (n + 1) / 2 + t] = 2.0 * c * s;
+        c = c * (n - t) / (t + 1);
+        s *= sgn;
+      }
+    }
+    bool first = true;
+    for (int x0 = xbeg; x0 < xend; x0 += xc) {
+      const int nx = std::min(xc, xend - x0);
+      const long ncol = (long)nx * nmo;
+      EpiBinomial epi{Z, eps_G + x0, nmom, PB, naux, nmo, ncol, bc};
+      AGroupedMoments A{Wmom, nmom, PB, naux, BM};
+      BRowMajor B{L + (long)x0 * nmo, (long)nmo * nmo, 0};
+      MGW_TRY((dgemm<BM, BN>(h, ngroups * BM, ncol, naux, 1, A, B, epi, "sigma_y_binomial")));
+      // Sigma(n) (+)= sum_{P,x} L[P][x][p] Z(n)[(P,x)][q]
+      AKMajor2 A2{L + (long)x0 * nmo, nx, (long)nmo * nmo, nmo, 0};
+      BRowMajor B2{Z, nmo, (long)naux * ncol};
+      EpiStore e2{sig, nmo, (long)nmo * nmo, 1.0, first ? 0.0 : 1.0};
+      MGW_TRY((dgemm<64, 64>(h, nmo, nmo, (long)naux * nx, nmom, A2, B2, e2, "sigma_gemm2")));
+      first = false;
+    }
+    if (first) MGW_CUDA(h, cudaMemsetAsync(sig, 0, sizeof(double) * nmom * nmo * nmo, h->stream));
+  }
+  return MGW_OK;
+}

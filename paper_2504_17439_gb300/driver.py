@@ -1,0 +1,62 @@
+"""Host-side composition of the library calls: one-shot G0W0 (Algorithm 1)
+and eigenvalue self-consistency (evGW, Algorithm 3).
+
+Every numerical step runs in libmgw through the binding in mgw.py; this
+module only sequences the calls and moves a few scalars.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import mgw
+
+
+def g0w0(h: mgw.Handle, eps_G: torch.Tensor, L: torch.Tensor, nocc: int, nmom_max: int,
+         screening: int = mgw.MGW_TDA, eps_W: torch.Tensor | None = None, fock: torch.Tensor | None = None,
+         opts: mgw.Options | None = None, Lov: torch.Tensor | None = None, want_chi: bool = False) -> dict:
+    """Response moments -> W -> Sigma(n,<), Sigma(n,>) -> block Lanczos per
+    sector -> H~ eigensolve, QP energies, Aufbau.  All tensors on the GPU."""
+    naux, nmo = L.shape[0], L.shape[1]
+    nvir = nmo - nocc
+    nmom = 2 * nmom_max + 2
+    nblk = nmom_max + 1
+    o = opts if opts is not None else mgw.options()
+    o.screening = screening
+    if Lov is None:
+        Lov = h.mgw_extract_ov(nocc, nvir, L)
+    Wmom = h.mgw_response_moments(o, nocc, nvir, naux, nmom, eps_G if eps_W is None else eps_W, Lov)
+    sh, sp = h.mgw_sigma_moments(o, nocc, nvir, naux, nmom, eps_G, L, Wmom)
+    ch, ah, bh, rh = h.mgw_block_lanczos(o, nmo, nmom, sh)
+    cp, ap, bp, rp = h.mgw_block_lanczos(o, nmo, nmom, sp)
+    f = torch.diag(eps_G) if fock is None else fock
+    qp = h.mgw_qp_solve(o, nmo, nblk, rh, rp, f.contiguous(), (ch, ah, bh), (cp, ap, bp), 0.0, 2.0 * nocc,
+                        want_chi=want_chi)
+    return dict(W=Wmom, sigma_hole=sh, sigma_part=sp, hole=(ch, ah, bh, rh), part=(cp, ap, bp, rp), **qp)
+
+
+def evgw(h: mgw.Handle, eps: torch.Tensor, L: torch.Tensor, nocc: int, nmom_max: int,
+         screening: int = mgw.MGW_TDA, g0: bool = False, w0: bool = False, conv_e: float | None = None,
+         max_iter: int | None = None, opts: mgw.Options | None = None) -> dict:
+    """Eigenvalue self-consistency (Sec. III B): eps^G and/or eps^W take the
+    QP energies of Eq. 34 until they change by less than conv_e."""
+    o = opts if opts is not None else mgw.options()
+    conv = o.conv_e if conv_e is None else conv_e
+    iters = o.max_iter if max_iter is None else max_iter
+    nvir = L.shape[1] - nocc
+    Lov = h.mgw_extract_ov(nocc, nvir, L)
+    fock = torch.diag(eps).contiguous()
+    epsG, epsW = eps.clone(), eps.clone()
+    hist = []
+    for it in range(iters):
+        r = g0w0(h, epsG, L, nocc, nmom_max, screening, eps_W=epsW, fock=fock, opts=o, Lov=Lov)
+        e_new = r["eps_qp"]
+        dG = 0.0 if g0 else float((e_new - epsG).abs().max())
+        dW = 0.0 if w0 else float((e_new - epsW).abs().max())
+        hist.append(max(dG, dW))
+        if not g0:
+            epsG = e_new.clone()
+        if not w0:
+            epsW = e_new.clone()
+        if max(dG, dW) < conv:
+            return dict(eps_qp=e_new, iterations=it + 1, converged=True, history=hist)
+    return dict(eps_qp=e_new, iterations=iters, converged=False, history=hist)

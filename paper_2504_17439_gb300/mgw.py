@@ -1,0 +1,240 @@
+"""Thin Python binding of libmgw (ctypes).
+
+Argument marshalling only: every function checks tensor device, dtype, shape
+and contiguity, passes raw device pointers and the handle's stream to the C
+ABI of include/mgw.h, and raises MgwError on a non-zero status.  All
+arithmetic runs in the library's CUDA kernels; there is no other path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+MGW_TDA, MGW_RPA = 0, 1
+MGW_FP64, MGW_BF16X3 = 0, 1
+
+_STATUS = {
+    0: "MGW_OK", -1: "MGW_ERR_ARG", -2: "MGW_ERR_CUDA", -3: "MGW_ERR_NOMEM", -4: "MGW_ERR_NOT_PD",
+    -5: "MGW_ERR_BREAKDOWN", -6: "MGW_ERR_NO_CONV", -7: "MGW_ERR_TIMEOUT", -8: "MGW_ERR_UNSUPPORTED",
+}
+
+
+class MgwError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("screening", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("nquad", ctypes.c_int),
+        ("xchunk", ctypes.c_int),
+        ("rank_tol", ctypes.c_double),
+        ("max_iter", ctypes.c_int),
+        ("conv_e", ctypes.c_double),
+        ("conv_mom", ctypes.c_double),
+        ("diis_space", ctypes.c_int),
+    ]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+
+# name -> argtypes after the handle
+_SIGS = {
+    "mgw_extract_ov": [_I, _I, _I, _P, _P],
+    "mgw_response_moments": [_P, _I, _I, _I, _I, _P, _P, _P],
+    "mgw_sigma_moments": [_P, _I, _I, _I, _I, _P, _P, _P, _P, _P],
+    "mgw_block_lanczos": [_P, _I, _I, _P, _P, _P, _P, ctypes.POINTER(_I)],
+    "mgw_qp_solve": [_P, _I, _I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _D, _D, _P, _P, _P, _P, _P,
+                     ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I)],
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libmgw.so (built by paper_2504_17439_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libmgw.so not built ({path}); run paper_2504_17439_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    lib.mgw_options_default.argtypes = [ctypes.POINTER(Options)]
+    lib.mgw_options_default.restype = None
+    lib.mgw_create.argtypes = [ctypes.POINTER(_P), _I, _P]
+    lib.mgw_create.restype = _I
+    lib.mgw_destroy.argtypes = [_P]
+    lib.mgw_destroy.restype = _I
+    lib.mgw_set_stream.argtypes = [_P, _P]
+    lib.mgw_set_stream.restype = _I
+    lib.mgw_last_error.argtypes = [_P]
+    lib.mgw_last_error.restype = ctypes.c_char_p
+    lib.mgw_workspace_bytes.argtypes = [_P]
+    lib.mgw_workspace_bytes.restype = ctypes.c_size_t
+    lib.mgw_profile.argtypes = [_P, _I]
+    lib.mgw_profile.restype = _I
+    lib.mgw_profile_query.argtypes = [_P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(_D)]
+    lib.mgw_profile_query.restype = _I
+    lib.mgw_launch_count.argtypes = [_P]
+    lib.mgw_launch_count.restype = ctypes.c_long
+    for name, args in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = [_P] + args
+        fn.restype = _I
+    _lib = lib
+    return lib
+
+
+def options(**kw) -> Options:
+    o = Options()
+    load().mgw_options_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t: torch.Tensor | None, shape=None, name="tensor"):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float64:
+        raise ValueError(f"{name} must be float64")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Handle:
+    """A libmgw handle bound to one device and the current torch stream."""
+
+    def __init__(self, device: int | None = None, stream: torch.cuda.Stream | None = None):
+        lib = load()
+        self._lib = lib
+        self.device = torch.cuda.current_device() if device is None else device
+        stream = stream or torch.cuda.current_stream(self.device)
+        self.stream = stream
+        h = ctypes.c_void_p()
+        st = lib.mgw_create(ctypes.byref(h), self.device, ctypes.c_void_p(stream.cuda_stream))
+        if st != 0:
+            raise MgwError(st, "mgw_create failed")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mgw_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream: torch.cuda.Stream):
+        self.stream = stream
+        self._check(self._lib.mgw_set_stream(self._h, ctypes.c_void_p(stream.cuda_stream)))
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(self._lib.mgw_workspace_bytes(self._h))
+
+    def profile(self, enable: bool):
+        self._check(self._lib.mgw_profile(self._h, 1 if enable else 0))
+
+    def profile_query(self, name: str = "*"):
+        """(launches, total milliseconds) of the recorded kernels named `name`."""
+        c, t = ctypes.c_long(), ctypes.c_double()
+        self._check(self._lib.mgw_profile_query(self._h, name.encode(), ctypes.byref(c), ctypes.byref(t)))
+        return c.value, t.value
+
+    @property
+    def launches(self) -> int:
+        return int(self._lib.mgw_launch_count(self._h))
+
+    def _check(self, st: int):
+        if st != 0:
+            raise MgwError(st, (self._lib.mgw_last_error(self._h) or b"").decode())
+
+    # -- the ABI entry points, same names ---------------------------------
+    def mgw_extract_ov(self, nocc, nvir, L, Lov=None):
+        naux, nmo = L.shape[0], L.shape[1]
+        Lov = Lov if Lov is not None else torch.empty((naux, nocc * nvir), dtype=L.dtype, device=L.device)
+        self._check(self._lib.mgw_extract_ov(self._h, nocc, nvir, naux, _ptr(L, (naux, nmo, nmo), "L"),
+                                             _ptr(Lov, (naux, nocc * nvir), "Lov")))
+        return Lov
+
+    def mgw_response_moments(self, opts: Options, nocc, nvir, naux, nmom, eps_W, Lov, Wmom=None):
+        Wmom = Wmom if Wmom is not None else torch.empty((nmom, naux, naux), dtype=torch.float64, device=Lov.device)
+        self._check(self._lib.mgw_response_moments(
+            self._h, ctypes.byref(opts), nocc, nvir, naux, nmom, _ptr(eps_W, (nocc + nvir,), "eps_W"),
+            _ptr(Lov, (naux, nocc * nvir), "Lov"), _ptr(Wmom, (nmom, naux, naux), "Wmom")))
+        return Wmom
+
+    def mgw_sigma_moments(self, opts: Options, nocc, nvir, naux, nmom, eps_G, L, Wmom, sig_hole=None, sig_part=None):
+        nmo = nocc + nvir
+        dev = L.device
+        sig_hole = sig_hole if sig_hole is not None else torch.empty((nmom, nmo, nmo), dtype=torch.float64, device=dev)
+        sig_part = sig_part if sig_part is not None else torch.empty((nmom, nmo, nmo), dtype=torch.float64, device=dev)
+        self._check(self._lib.mgw_sigma_moments(
+            self._h, ctypes.byref(opts), nocc, nvir, naux, nmom, _ptr(eps_G, (nmo,), "eps_G"),
+            _ptr(L, (naux, nmo, nmo), "L"), _ptr(Wmom, (nmom, naux, naux), "Wmom"),
+            _ptr(sig_hole, (nmom, nmo, nmo), "sig_hole"), _ptr(sig_part, (nmom, nmo, nmo), "sig_part")))
+        return sig_hole, sig_part
+
+    def mgw_block_lanczos(self, opts: Options, nmo, nmom, sig, coup=None, alpha=None, beta=None):
+        nblk = nmom // 2
+        dev = sig.device
+        coup = coup if coup is not None else torch.empty((nmo, nmo), dtype=torch.float64, device=dev)
+        alpha = alpha if alpha is not None else torch.empty((nblk, nmo, nmo), dtype=torch.float64, device=dev)
+        if beta is None and nblk > 1:
+            beta = torch.empty((nblk - 1, nmo, nmo), dtype=torch.float64, device=dev)
+        rank = ctypes.c_int(0)
+        self._check(self._lib.mgw_block_lanczos(
+            self._h, ctypes.byref(opts), nmo, nmom, _ptr(sig, (nmom, nmo, nmo), "sig"), _ptr(coup, (nmo, nmo), "coup"),
+            _ptr(alpha, (nblk, nmo, nmo), "alpha"),
+            _ptr(beta, (nblk - 1, nmo, nmo), "beta") if nblk > 1 else None, ctypes.byref(rank)))
+        return coup, alpha, beta, rank.value
+
+    def mgw_qp_solve(self, opts: Options, nmo, nblk, rank_h, rank_p, fock, hole, part, zeta=0.0, nelec=0.0,
+                     want_chi=False, want_rho=True):
+        """hole/part: (coup, alpha, beta) as returned by mgw_block_lanczos."""
+        dim = nmo + nblk * (rank_h + rank_p)
+        dev = fock.device
+        E = torch.empty((dim,), dtype=torch.float64, device=dev)
+        weight = torch.empty((dim,), dtype=torch.float64, device=dev)
+        chi = torch.empty((nmo, dim), dtype=torch.float64, device=dev) if want_chi else None
+        eps_qp = torch.empty((nmo,), dtype=torch.float64, device=dev)
+        rho = torch.empty((nmo, nmo), dtype=torch.float64, device=dev) if want_rho else None
+        mu, ne, m = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+
+        def blk(t, shape, name):
+            return _ptr(t, shape, name) if t is not None else None
+        ch, ah, bh = hole
+        cp, ap, bp = part
+        self._check(self._lib.mgw_qp_solve(
+            self._h, ctypes.byref(opts), nmo, nblk, rank_h, rank_p, _ptr(fock, (nmo, nmo), "fock"),
+            blk(ch, (nmo, nmo), "coup_h"), blk(ah, (nblk, nmo, nmo), "alpha_h"),
+            blk(bh, (nblk - 1, nmo, nmo), "beta_h") if nblk > 1 else None,
+            blk(cp, (nmo, nmo), "coup_p"), blk(ap, (nblk, nmo, nmo), "alpha_p"),
+            blk(bp, (nblk - 1, nmo, nmo), "beta_p") if nblk > 1 else None,
+            float(zeta), float(nelec), _ptr(E), _ptr(weight), _ptr(chi), _ptr(eps_qp), _ptr(rho),
+            ctypes.byref(mu), ctypes.byref(ne), ctypes.byref(m)))
+        return dict(E=E, weight=weight, chi=chi, eps_qp=eps_qp, rho=rho, mu=mu.value, nelec=ne.value, m=m.value)

@@ -1,0 +1,212 @@
+"""GPU path (libmgw through its C ABI) against the CPU oracle, element by element.
+
+Tolerance of the FP64 path: 1e-9 relative in the Frobenius norm of every
+moment order / block, and 1e-9 Ha absolute on energies.  Each stage is also
+checked on inputs the oracle produced (so a stage is judged alone), and the
+whole chain is checked end to end.  Sizes span several tiles and ragged
+tails (naux, ov, nmo not multiples of the 64/96-row tiles).
+"""
+import numpy as np
+import pytest
+import torch
+
+import mgw_inputs
+from oracle import mgw_oracle as orc
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def h():
+    from paper_2504_17439_gb300 import build, mgw
+
+    build.build()
+    return mgw.Handle(0)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+SHAPES = [
+    # nocc, nvir, naux, nmom_max, seed
+    (5, 19, 72, 5, mgw_inputs.SEED_BASE),       # the 24-orbital workload
+    (3, 7, 65, 3, 11),                          # ragged tails on every tile edge
+    (1, 1, 1, 2, 12),                           # one particle-hole pair
+    (7, 30, 130, 4, 13),                        # several tiles in every direction
+]
+
+
+def system(nocc, nvir, naux, seed, scale=1.0):
+    eps = mgw_inputs.orbital_energies(nocc, nvir, seed)
+    L = mgw_inputs.df_tensor(naux, nocc + nvir, seed) * scale
+    return eps, L
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("screening", ["tda", "rpa"])
+def test_response_moments(h, shape, screening):
+    from paper_2504_17439_gb300 import mgw
+
+    nocc, nvir, naux, N, seed = shape
+    eps, L = system(nocc, nvir, naux, seed, scale=2.0)
+    nmom = 2 * N + 2
+    D = orc.energy_differences(eps, nocc)
+    Lov = orc.particle_hole_block(L, nocc)
+    ref = orc.response_moments(Lov, D, nmom, screening, 48)
+    o = mgw.options(screening=mgw.MGW_TDA if screening == "tda" else mgw.MGW_RPA)
+    got = host(h.mgw_response_moments(o, nocc, nvir, naux, nmom, dev(eps), dev(Lov)))
+    for n in range(nmom):
+        assert rel(got[n], ref[n]) < TOL, (n, rel(got[n], ref[n]))
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_extract_ov(h, shape):
+    nocc, nvir, naux, N, seed = shape
+    eps, L = system(nocc, nvir, naux, seed)
+    got = host(h.mgw_extract_ov(nocc, nvir, dev(L)))
+    assert np.array_equal(got, orc.particle_hole_block(L, nocc))
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("xchunk", [0, 3])
+def test_sigma_moments(h, shape, xchunk):
+    from paper_2504_17439_gb300 import mgw
+
+    nocc, nvir, naux, N, seed = shape
+    eps, L = system(nocc, nvir, naux, seed, scale=2.0)
+    nmom = 2 * N + 2
+    W = orc.tda_response_moments(orc.particle_hole_block(L, nocc), orc.energy_differences(eps, nocc), nmom)
+    rh, rp = orc.sigma_moments(eps, nocc, L, W)
+    o = mgw.options(xchunk=xchunk)
+    gh, gp = h.mgw_sigma_moments(o, nocc, nvir, naux, nmom, dev(eps), dev(L), dev(W))
+    gh, gp = host(gh), host(gp)
+    for n in range(nmom):
+        assert rel(gh[n], rh[n]) < TOL, ("hole", n, rel(gh[n], rh[n]))
+        assert rel(gp[n], rp[n]) < TOL, ("particle", n, rel(gp[n], rp[n]))
+
+
+@pytest.mark.parametrize("shape", SHAPES[:2] + SHAPES[3:])
+def test_block_lanczos_full_rank(h, shape):
+    from paper_2504_17439_gb300 import mgw
+
+    nocc, nvir, naux, N, seed = shape
+    eps, L = system(nocc, nvir, naux, seed, scale=2.0)
+    nmom = 2 * N + 2
+    W = orc.tda_response_moments(orc.particle_hole_block(L, nocc), orc.energy_differences(eps, nocc), nmom)
+    sh, sp = orc.sigma_moments(eps, nocc, L, W)
+    o = mgw.options()
+    for sig in (sh, sp):
+        coup, alpha, beta, r = orc.block_lanczos(sig, N + 1)
+        gc, ga, gb, gr = h.mgw_block_lanczos(o, eps.size, nmom, dev(sig))
+        assert gr == r == eps.size
+        assert rel(host(gc), coup) < TOL
+        for i in range(N + 1):
+            assert rel(host(ga)[i], alpha[i]) < 1e-8, ("alpha", i, rel(host(ga)[i], alpha[i]))
+        for i in range(N):
+            assert rel(host(gb)[i], beta[i]) < 1e-8, ("beta", i, rel(host(gb)[i], beta[i]))
+
+
+def test_block_lanczos_rank_deficient(h):
+    # one occupied orbital, two virtuals, two aux: Sigma_hole(0) has rank 2 < nmo = 3;
+    # blocks live in a basis fixed only up to signs, so compare what is unique:
+    # the moments they reproduce
+    from paper_2504_17439_gb300 import mgw
+
+    eps, L = system(1, 2, 2, 11, scale=3.0)
+    sh, _ = orc.sigma_moments(eps, 1, L, orc.tda_response_moments(
+        orc.particle_hole_block(L, 1), orc.energy_differences(eps, 1), 4))
+    coup, alpha, beta, r = orc.block_lanczos(sh, 2)
+    gc, ga, gb, gr = h.mgw_block_lanczos(mgw.options(), 3, 4, dev(sh))
+    assert gr == r == 2
+    gc, ga, gb = host(gc)[:, :2], host(ga)[:, :2, :2], host(gb)[:, :2, :2]
+    T = np.block([[ga[0], gb[0].T], [gb[0], ga[1]]])
+    Tn = np.eye(4)
+    for n in range(4):
+        assert rel(gc @ Tn[:2, :2] @ gc.T, sh[n]) < 1e-9
+        Tn = Tn @ T
+
+
+def test_zero_interaction(h):
+    from paper_2504_17439_gb300 import driver, mgw
+
+    eps = mgw_inputs.orbital_energies(3, 5, 3)
+    L = np.zeros((6, 8, 8))
+    r = driver.g0w0(h, dev(eps), dev(L), 3, 2)
+    assert np.all(host(r["sigma_hole"]) == 0) and np.all(host(r["sigma_part"]) == 0)
+    assert r["hole"][3] == 0 and r["part"][3] == 0
+    assert np.array_equal(host(r["eps_qp"]), eps)
+
+
+@pytest.mark.parametrize("shape", SHAPES[:2] + SHAPES[3:])
+def test_qp_solve_on_oracle_blocks(h, shape):
+    from paper_2504_17439_gb300 import mgw
+
+    nocc, nvir, naux, N, seed = shape
+    eps, L = system(nocc, nvir, naux, seed, scale=2.0)
+    ref = orc.g0w0(eps, L, nocc, N)
+    hole, part = ref["hole"], ref["part"]
+    nmo = eps.size
+
+    def blocks(b):
+        return dev(b[0]), dev(b[1]), dev(b[2]) if N > 0 else None
+    got = h.mgw_qp_solve(mgw.options(), nmo, N + 1, hole[3], part[3], dev(np.diag(eps)), blocks(hole),
+                         blocks(part), 0.0, 2.0 * nocc)
+    assert np.abs(host(got["E"]) - ref["E"]).max() < 1e-9
+    assert np.abs(host(got["weight"]) - ref["weight"]).max() < 1e-9
+    assert np.abs(host(got["eps_qp"]) - ref["eps_qp"]).max() < 1e-9
+    assert got["m"] == ref["m"]
+    assert abs(got["mu"] - ref["mu"]) < 1e-9 and abs(got["nelec"] - ref["nelec"]) < 1e-9
+    assert np.abs(host(got["rho"]) - ref["rho"]).max() < 1e-9
+
+
+@pytest.mark.parametrize("screening", ["tda", "rpa"])
+def test_g0w0_end_to_end(h, screening):
+    from paper_2504_17439_gb300 import driver, mgw
+
+    shape, seed = mgw_inputs.workload("g0w0-nmo24-naux72")
+    eps, L = mgw_inputs.system(shape, seed)
+    ref = orc.g0w0(eps, L, shape.nocc, shape.nmom_max, screening)
+    r = driver.g0w0(h, dev(eps), dev(L), shape.nocc, shape.nmom_max,
+                    mgw.MGW_TDA if screening == "tda" else mgw.MGW_RPA)
+    for n in range(shape.nmom):
+        assert rel(host(r["sigma_hole"])[n], ref["sigma_hole"][n]) < TOL
+        assert rel(host(r["sigma_part"])[n], ref["sigma_part"][n]) < TOL
+    assert np.abs(host(r["eps_qp"]) - ref["eps_qp"]).max() < 1e-8
+    assert np.abs(host(r["E"]) - ref["E"]).max() < 1e-8
+    assert abs(r["mu"] - ref["mu"]) < 1e-8
+
+
+def test_evgw_matches_oracle(h):
+    from paper_2504_17439_gb300 import driver
+
+    eps, L = system(3, 9, 40, 21, scale=2.0)
+    ref = orc.evgw(eps, L, 3, 2, conv_e=1e-8, max_iter=40)
+    got = driver.evgw(h, dev(eps), dev(L), 3, 2, conv_e=1e-8, max_iter=40)
+    assert got["converged"] and ref["converged"]
+    assert got["iterations"] == ref["iterations"]
+    assert np.abs(host(got["eps_qp"]) - ref["eps_qp"]).max() < 1e-8
+
+
+def test_bad_arguments_return_status(h):
+    from paper_2504_17439_gb300 import mgw
+
+    with pytest.raises(mgw.MgwError) as ei:
+        h.mgw_sigma_moments(mgw.options(), 2, 2, 3, 30, dev(np.zeros(4)), dev(np.zeros((3, 4, 4))),
+                            dev(np.zeros((30, 3, 3))))
+    assert ei.value.status == -1
+    with pytest.raises(mgw.MgwError) as ei:
+        h.mgw_response_moments(mgw.options(screening=1, nquad=7), 1, 1, 1, 2, dev(np.array([-1.0, 1.0])),
+                               dev(np.ones((1, 1))))
+    assert ei.value.status == -1

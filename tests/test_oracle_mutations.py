@@ -93,10 +93,13 @@ CASES = [
     (["rpa_eta0"], "(np.linalg.inv(eye + Q) - eye)", "(np.linalg.inv(eye + Q) + eye)", "sigma", "rpa"),
     (["rpa_eta0"], "S = eye + 4.0 *", "S = eye - 4.0 *", "sigma", "rpa"),
     (["sigma_moments"], "sign = -1.0 if hole else 1.0", "sign = 1.0", "sigma", "tda"),
-    (["sigma_moments"], "out[n] += 2.0 *", "out[n] += 1.0 *", "sigma", "tda"),
-    (["sigma_moments"], "eps[x] ** (n - t) * Wx[t]", "eps[x] ** (n - t) * Wx[n]", "sigma", "tda"),
+    (["sigma_moments"], "wgt = 2.0 *", "wgt = 1.0 *", "sigma", "tda"),
+    # the W^(n) index printed inside the t-sum of Eqs. 6-7
+    (["sigma_moments"], "out[n] += np.tensordot(wgt, Wx[xs], axes=1)",
+     "out[n] += np.tensordot(wgt, ((Lxp @ W[n]) @ Lx)[xs], axes=1)", "sigma", "tda"),
     (["sigma_moments"], "math.comb(n, t)", "1", "sigma", "tda"),
-    (["sigma_moments"], "Lxp.T @ W[t] @ Lx", "Lxp.T @ W[t] @ Lx * (1 + 0.01)", "sigma", "tda"),
+    (["sigma_moments"], "eps[xs] ** (n - t)", "eps[xs] ** t", "sigma", "tda"),
+    (["sigma_moments"], "Wx = (Lxp @ W[t]) @ Lx", "Wx = (Lxp @ W[t]) @ Lx * (1 + 0.01)", "sigma", "tda"),
     (["block_lanczos"], "Rk -= C[i][k] @ a", "Rk -= a @ C[i][k] * 0.5", "lanczos", None),
     (["block_lanczos"], "Rk -= C[i - 1][k] @ beta[i - 1].T", "Rk -= C[i - 1][k] @ beta[i - 1].T * 0.0", "lanczos", None),
     (["block_lanczos"], "acc += Xk.T @ Sh[k + l + m] @ Yl", "acc += Xk.T @ Sh[k + l] @ Yl", "lanczos", None),
@@ -120,7 +123,7 @@ def test_pins_catch_planted_mistake(case):
 
 
 def test_unmutated_copy_passes_every_pin():
-    mod = mutant(["sigma_moments"], "out[n] += 2.0 *", "out[n] += 2.0 *")
+    mod = mutant(["sigma_moments"], "wgt = 2.0 *", "wgt = 2.0 *")
     assert sigma_pin_error(mod, "tda") < 1e-10
     assert sigma_pin_error(mod, "rpa") < 1e-9
     assert lanczos_pin_error(mod) < 1e-9

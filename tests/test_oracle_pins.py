@@ -296,3 +296,12 @@ def test_evgw_reaches_a_fixed_point():
     # at the fixed point the QP energies regenerate themselves
     r = orc.g0w0(out["eps_qp"], L, 3, 2, fock=np.diag(eps))
     assert np.abs(r["eps_qp"] - out["eps_qp"]).max() < 1e-8
+
+
+def test_tda_rows_subset_matches_full():
+    eps, L = small_system()
+    D = orc.energy_differences(eps, 3)
+    Lov = orc.particle_hole_block(L, 3)
+    W = orc.tda_response_moments(Lov, D, 6)
+    Wr = orc.tda_response_moments(Lov, D, 6, rows=[0, 5, 11])
+    assert np.allclose(Wr, W[:, [0, 5, 11]], rtol=1e-13, atol=1e-16)
