@@ -189,6 +189,18 @@ mgw_status mgw_qp_solve(mgw_handle* h, const mgw_options* o,
                         double* eps_qp, double* rho,
                         double* mu_host, double* nelec_host, int* m_host);
 
+/*
+ * mgw_gemm_bf16x3 -- C = A B^T on the tensor cores (tcgen05, TMA, TMEM):
+ * each FP64 operand is split as x = hi + lo with hi = bf16(x),
+ * lo = bf16(x - hi), and C accumulates hi*hi + hi*lo + lo*hi in FP32, then is
+ * written as FP64.  The split-precision product of the mixed path; relative
+ * error about 1e-5 of |A||B| per element.  Not in the paper (its contractions
+ * are FP64); the building block of the precision pattern.
+ *   A [M][K], B [N][K] in (FP64, row-major);  C [M][N] out (FP64)
+ */
+mgw_status mgw_gemm_bf16x3(mgw_handle* h, int M, int N, int K,
+                           const double* A, const double* B, double* C);
+
 #ifdef __cplusplus
 }
 #endif

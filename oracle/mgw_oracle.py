@@ -25,7 +25,8 @@ garbled are listed in the docstrings that use them:
       integrals use the same nodes.
   R5  Block Lanczos normalisation: symmetric (PSD) square roots for Sigma(0)
       and every beta, so the blocks are unique; inverse square roots drop
-      eigenvalues below rank_tol * lambda_max.  Moments are centred by
+      eigenvalues below rank_tol * lambda_max (for beta, of the normalised
+      residual, below rank_tol * max(lambda_max, 1); beta = 0 ends the chain).  Moments are centred by
       c = tr Sigma(1) / tr Sigma(0) and scaled by
       s = (tr M(2N) / tr M(0))^(1/2N) before the recursion (exact in
       exact arithmetic; undone on the returned blocks).
@@ -192,11 +193,11 @@ def sigma_moments(eps: np.ndarray, nocc: int, L: np.ndarray, W: np.ndarray, rows
 # Block Lanczos from moments (the upfolded effective Hamiltonian of Eq. 9)
 
 
-def _psd_sqrt(S, rank_tol):
+def _psd_sqrt(S, rank_tol, floor=0.0):
     """Symmetric square root and pseudo-inverse square root of a symmetric
-    PSD matrix, dropping eigenvalues below rank_tol * lambda_max."""
+    PSD matrix, dropping eigenvalues below rank_tol * max(lambda_max, floor)."""
     lam, U = np.linalg.eigh(0.5 * (S + S.T))
-    lmax = max(lam.max(), 0.0) if lam.size else 0.0
+    lmax = max(lam.max(), 0.0, floor) if lam.size else 0.0
     keep = lam > rank_tol * lmax if lmax > 0 else np.zeros_like(lam, dtype=bool)
     r = int(keep.sum())
     lk, Uk = lam[keep], U[:, keep]
@@ -267,7 +268,10 @@ def block_lanczos(sig: np.ndarray, nblk: int, rank_tol: float = 1e-12):
                 Rk -= C[i - 1][k] @ beta[i - 1].T
             R.append(Rk)
         RR = inner(R, R, 0)
-        b, binv, _, _, _ = _psd_sqrt(RR, rank_tol)
+        # the residual lives in the normalised, unit-scaled problem, so its rank is
+        # judged against max(lambda_max, 1): a vanishing residual (every pole
+        # already represented) gives beta = 0 and a decoupled remainder
+        b, binv, _, _, _ = _psd_sqrt(RR, rank_tol, floor=1.0)
         beta.append(b)
         C.append([Rk @ binv for Rk in R])
     alpha = [s * a + c * eye for a in alpha]

@@ -83,14 +83,14 @@ static unsigned nb(long n) { return (unsigned)((n + 255) / 256); }
 
 struct PsdRoot {
   // symmetric square root and pseudo-inverse square root of an r x r PSD matrix
-  static mgw_status run(mgw_handle* h, int r, const double* S, double rank_tol, double* sq, double* isq,
-                        double* evec, double* lam, double* tmp, int* rank_out) {
+  static mgw_status run(mgw_handle* h, int r, const double* S, double rank_tol, double floor, double* sq,
+                        double* isq, double* evec, double* lam, double* tmp, int* rank_out) {
     MGW_CUDA(h, cudaMemcpyAsync(evec, S, sizeof(double) * r * r, cudaMemcpyDeviceToDevice, h->stream));
     MGW_TRY(syevd(h, r, evec, lam));
     std::vector<double> hl(r);
     MGW_CUDA(h, cudaMemcpyAsync(hl.data(), lam, sizeof(double) * r, cudaMemcpyDeviceToHost, h->stream));
     MGW_CUDA(h, cudaStreamSynchronize(h->stream));
-    double lmax = std::max(hl[r - 1], 0.0);
+    double lmax = std::max(std::max(hl[r - 1], 0.0), floor);
     int kept = 0;
     for (int i = 0; i < r; ++i)
       if (lmax > 0 && hl[i] > rank_tol * lmax) ++kept;
@@ -261,8 +261,9 @@ extern "C" mgw_status mgw_block_lanczos(mgw_handle* h, const mgw_options* o, int
     }
     MGW_TRY(inner(Rl, Rl, 0, RR));
     int rb = 0;
-    MGW_TRY(PsdRoot::run(h, r, RR, o->rank_tol, hbeta[i + 1], sq, evec, lam, tmp2, &rb));
-    if (rb == 0) return fail(h, MGW_ERR_BREAKDOWN, "mgw_block_lanczos: zero residual at block %d", i + 1);
+    // rank of the normalised residual judged against max(lambda_max, 1); a
+    // vanishing residual gives beta = 0 and a decoupled remainder of the chain
+    MGW_TRY(PsdRoot::run(h, r, RR, o->rank_tol, 1.0, hbeta[i + 1], sq, evec, lam, tmp2, &rb));
     for (int k = 0; k <= i + 1; ++k) MGW_TRY(gemm_nn(h, r, r, r, 1.0, Rl[k], r, sq, r, 0.0, C[i + 1][k], r));
   }
 

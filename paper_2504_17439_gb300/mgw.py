@@ -51,6 +51,7 @@ _D = ctypes.c_double
 # name -> argtypes after the handle
 _SIGS = {
     "mgw_extract_ov": [_I, _I, _I, _P, _P],
+    "mgw_gemm_bf16x3": [_I, _I, _I, _P, _P, _P],
     "mgw_response_moments": [_P, _I, _I, _I, _I, _P, _P, _P],
     "mgw_sigma_moments": [_P, _I, _I, _I, _I, _P, _P, _P, _P, _P],
     "mgw_block_lanczos": [_P, _I, _I, _P, _P, _P, _P, ctypes.POINTER(_I)],
@@ -174,6 +175,15 @@ class Handle:
             raise MgwError(st, (self._lib.mgw_last_error(self._h) or b"").decode())
 
     # -- the ABI entry points, same names ---------------------------------
+    def mgw_gemm_bf16x3(self, A, B, C=None):
+        """C = A B^T on the tensor cores with BF16 hi/lo operand splits (3 products, FP32 accumulate)."""
+        M, K = A.shape
+        N = B.shape[0]
+        C = C if C is not None else torch.empty((M, N), dtype=torch.float64, device=A.device)
+        self._check(self._lib.mgw_gemm_bf16x3(self._h, M, N, K, _ptr(A, (M, K), "A"), _ptr(B, (N, K), "B"),
+                                              _ptr(C, (M, N), "C")))
+        return C
+
     def mgw_extract_ov(self, nocc, nvir, L, Lov=None):
         naux, nmo = L.shape[0], L.shape[1]
         Lov = Lov if Lov is not None else torch.empty((naux, nocc * nvir), dtype=L.dtype, device=L.device)

@@ -1,0 +1,32 @@
+"""Tensor-core (tcgen05/TMA/TMEM) split-precision GEMM against an FP64 product.
+
+The error bound follows from the arithmetic: with x = hi + lo, |lo| <= 2^-9 |x|
+and |x - hi - lo| <= 2^-9 |lo|, the dropped lo*lo term and the split residues
+are ~2^-16 |A||B| per product, plus FP32 accumulation (2^-24 sqrt(K)); the
+test allows 2e-5 of sum_k |A_ik||B_jk|.
+"""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def h():
+    from paper_2504_17439_gb300 import build, mgw
+
+    build.build()
+    return mgw.Handle(0)
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 256, 64), (300, 520, 200), (1, 1, 1), (257, 17, 1000), (1024, 1024, 4800)])
+def test_bf16x3_gemm_matches_fp64(h, M, N, K):
+    g = np.random.default_rng(M * 7 + N * 3 + K)
+    A = g.standard_normal((M, K))
+    B = g.standard_normal((N, K))
+    C = h.mgw_gemm_bf16x3(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()).cpu().numpy()
+    ref = A @ B.T
+    scale = np.abs(A) @ np.abs(B).T
+    err = np.abs(C - ref) / scale
+    assert err.max() < 2e-5, err.max()
