@@ -237,8 +237,10 @@ def run_gpu(args):
     clocks.start()
     barrier()
     t_wall = time.perf_counter()
+    torch.cuda.cudart().cudaProfilerStart()  # a profiler started with capture off records this region only
     recs = [step()[0] for _ in range(args.steps)]
     barrier()
+    torch.cuda.cudart().cudaProfilerStop()
     t_wall = time.perf_counter() - t_wall
     clk = clocks.stop()
     launches = h.launches - launches0
