@@ -405,3 +405,148 @@ def evgw(eps, L, nocc, nmom_max, screening="tda", nq=48, g0=False, w0=False,
         if max(dG, dW) < conv_e:
             return dict(eps_qp=e_new, iterations=it + 1, converged=True, history=hist)
     return dict(eps_qp=e_new, iterations=max_iter, converged=False, history=hist)
+
+
+# ----------------------------------------------------------------------------
+# Fock self-consistency (fsGW), Algorithm 2 / Sec. III F
+#
+# Readings (the paper states the loops, not their numerics):
+#  F1  All static quantities live in the fixed basis of the reference
+#      orbitals; the self-energy built in the current orbitals C is carried
+#      there by its coupling rows: W~_ref = C W~_mo (Sigma_ref = C Sigma_mo C^T).
+#  F2  F[rho] = h + J[rho] - K[rho]/2 with rho the spin-summed correlated
+#      density of Eq. 40 (Tr rho = N), J_pq = sum_P L_Ppq sum_rs L_Prs rho_rs,
+#      K_pq = sum_P sum_rs L_Ppr rho_rs L_Psq.
+#  F3  zeta: golden-section search on [-1, 1] Ha of |N(zeta) - N| (the
+#      Aufbau count of Eq. 40 for H~(zeta)), at most 60 evaluations, stopping
+#      when the bracket is below 1e-8 Ha or the count is met to 1e-10.
+#  F4  Fock loop at fixed zeta: Pulay DIIS on F with error F[rho(F)] - F
+#      (space 12, Sec. IV B), plain iteration for the first two steps, until
+#      max |delta rho| < 1e-8 (at most 100 steps).
+#  F5  Outer loop: zeta search then Fock loop, repeated (at most 20 times)
+#      until the electron count and the density are both consistent; then
+#      eps, C <- eigh(F); the next self-energy is built in the new orbitals.
+#  F6  QP energies (Eq. 34) are assigned per orbital of the current F (its
+#      eigenvectors), the basis in which Eq. 34 names the orbitals p.
+
+
+def fock_build(h, L, rho):
+    """F[rho] = h + J[rho] - K[rho]/2 (reading F2)."""
+    J = np.einsum("Ppq,P->pq", L, np.einsum("Prs,rs->P", L, rho))
+    K = np.einsum("Ppr,rs,Psq->pq", L, rho, L, optimize=True)
+    return h + J - 0.5 * K
+
+
+def rotate_df(L, C):
+    """L'_Q = C^T L_Q C: the DF tensor in the orbitals C (Algorithm 1's
+    transformed copy V^_Qpx, from the reference basis instead of AOs)."""
+    return np.einsum("ap,Qab,bq->Qpq", C, L, C, optimize=True)
+
+
+def zeta_search(F, hole, part, nelec, lo=-1.0, hi=1.0, max_eval=60, tol=1e-8):
+    """Reading F3: golden section on |N(zeta) - N|."""
+    g = (math.sqrt(5.0) - 1.0) / 2.0
+
+    def f(z):
+        return abs(qp_solve(F, hole, part, nelec, z)["nelec"] - nelec)
+    a, b = lo, hi
+    c, d = b - g * (b - a), a + g * (b - a)
+    fc, fd = f(c), f(d)
+    evals = 2
+    while b - a > tol and evals < max_eval and min(fc, fd) > 1e-10:
+        if fc <= fd:
+            b, d, fd = d, c, fc
+            c = b - g * (b - a)
+            fc = f(c)
+        else:
+            a, c, fc = c, d, fd
+            d = a + g * (b - a)
+            fd = f(d)
+        evals += 1
+    return (c, fc) if fc <= fd else (d, fd)
+
+
+def diis_extrapolate(Fs, errs):
+    """Pulay DIIS: minimise |sum_i c_i e_i| with sum_i c_i = 1."""
+    n = len(Fs)
+    B = np.zeros((n + 1, n + 1))
+    for i in range(n):
+        for j in range(n):
+            B[i, j] = np.vdot(errs[i], errs[j])
+    B[n, :n] = B[:n, n] = -1.0
+    rhs = np.zeros(n + 1)
+    rhs[n] = -1.0
+    c = np.linalg.lstsq(B, rhs, rcond=None)[0][:n]
+    return sum(ci * Fi for ci, Fi in zip(c, Fs))
+
+
+def fock_loop(h, L, F, hole, part, nelec, zeta, diis_space=12, max_iter=100, tol=1e-8):
+    """Reading F4.  Returns (F, rho, iterations)."""
+    Fs, errs = [], []
+    rho_old = None
+    rho = None
+    for it in range(max_iter):
+        rho = qp_solve(F, hole, part, nelec, zeta)["rho"]
+        Fn = fock_build(h, L, rho)
+        if rho_old is not None and np.abs(rho - rho_old).max() < tol:
+            return Fn, rho, it + 1
+        rho_old = rho
+        Fs.append(Fn)
+        errs.append(Fn - F)
+        Fs, errs = Fs[-diis_space:], errs[-diis_space:]
+        F = Fn if it < 2 else diis_extrapolate(Fs, errs)
+    return F, rho, max_iter
+
+
+def fsgw(h, L, eps, nocc, nmom_max, screening="tda", nq=48, max_outer=30, conv_e=5.0 * 3.6749322e-5,
+         conv_mom=1e-4, diis_space=12, F0=None):
+    """Algorithm 2.  h, L in the reference orbital basis; eps the reference
+    energies (F[rho_HF] = diag(eps) by the construction of h), or a starting
+    Fock matrix F0 in the same basis (its eigenpairs give the first orbitals).
+    Returns the converged QP energies, F, zeta and iteration counts."""
+    nelec = 2.0 * nocc
+    F = np.diag(eps).astype(float) if F0 is None else np.array(F0, dtype=float)
+    e, C = (eps.copy(), np.eye(eps.size)) if F0 is None else np.linalg.eigh(F)
+    zeta = 0.0
+    prev_sig = None
+    prev_qp = None
+    history = []
+    for outer in range(max_outer):
+        Lm = rotate_df(L, C)
+        nmom = 2 * nmom_max + 2
+        D = energy_differences(e, nocc)
+        W = response_moments(particle_hole_block(Lm, nocc), D, nmom, screening, nq)
+        sh, sp = sigma_moments(e, nocc, Lm, W)
+        hole = block_lanczos(sh, nmom_max + 1)
+        part = block_lanczos(sp, nmom_max + 1)
+        # carry the chains' coupling into the reference basis (F1)
+        hole_r = (C @ hole[0], hole[1], hole[2])
+        part_r = (C @ part[0], part[1], part[2])
+        sig_ref = np.stack([C @ (a + b) @ C.T for a, b in zip(sh, sp)])
+        inner = 0
+        for rep in range(20):
+            zeta, nerr = zeta_search(F, hole_r, part_r, nelec)
+            F, rho, k = fock_loop(h, L, F, hole_r, part_r, nelec, zeta, diis_space)
+            inner += k
+            n_now = qp_solve(F, hole_r, part_r, nelec, zeta)["nelec"]
+            if abs(n_now - nelec) <= max(nerr, 1e-10) + 1e-12 and k <= 2:
+                break
+        e, C = np.linalg.eigh(F)
+        # QP assignment in the eigenbasis of F (F6)
+        qp = qp_solve(C.T @ F @ C, (C.T @ hole_r[0], hole[1], hole[2]), (C.T @ part_r[0], part[1], part[2]),
+                      nelec, zeta)
+        dsig = np.abs(sig_ref - prev_sig).max() if prev_sig is not None else np.inf
+        dqp = np.abs(qp["eps_qp"] - prev_qp).max() if prev_qp is not None else np.inf
+        history.append(dict(outer=outer, inner=inner, zeta=zeta, dsig=dsig, dqp=dqp, nelec=qp["nelec"]))
+        prev_sig, prev_qp = sig_ref, qp["eps_qp"]
+        if dsig < conv_mom and dqp < conv_e:
+            return dict(eps_qp=qp["eps_qp"], F=F, zeta=zeta, converged=True, history=history, mu=qp["mu"])
+    return dict(eps_qp=qp["eps_qp"], F=F, zeta=zeta, converged=False, history=history, mu=qp["mu"])
+
+
+def hf_core_hamiltonian(eps, L, nocc):
+    """h = diag(eps) - J[rho_HF] + K[rho_HF]/2 so that F[rho_HF] = diag(eps)
+    (the synthetic reference is a canonical Hartree-Fock state)."""
+    rho = np.zeros((eps.size, eps.size))
+    rho[np.arange(nocc), np.arange(nocc)] = 2.0
+    return np.diag(eps) - (fock_build(np.zeros_like(rho), L, rho))
