@@ -41,6 +41,15 @@ import mgw_inputs  # noqa: E402
 WORKLOAD = "g0w0-nmo400-naux1600"
 METRIC = "sigma_moment_build_s"
 FP64_PEAK_GFLOPS = 1250.0  # nominal GB300 FP64 (DFMA) rate; the ALU bound of the FP64 path
+DIGIT_PRODUCTS = 28        # BF16 digit products per FP64-accurate tensor-core product (7 digits, levels <= 8)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
 
 
 def env_int(name, default):
@@ -202,7 +211,10 @@ def run_gpu(args):
     L = L_h.cuda()
     stream = torch.cuda.current_stream()
     h = mgw.Handle(local, stream)
-    o = mgw.options(screening=mgw.MGW_TDA if args.screening == "tda" else mgw.MGW_RPA)
+    o = mgw.options(screening=mgw.MGW_TDA if args.screening == "tda" else mgw.MGW_RPA,
+                    precision=mgw.MGW_FP64 if args.precision == "fp64" else mgw.MGW_FP64_TC)
+    tc = args.precision == "fp64_tc"
+    ykern = "sigma_y_binomial_tc" if tc else "sigma_y_binomial"
     Lov = torch.empty((naux, nocc * nvir), dtype=torch.float64, device="cuda")
     W = torch.empty((nmom, naux, naux), dtype=torch.float64, device="cuda")
     sh = torch.empty((nmom, nmo, nmo), dtype=torch.float64, device="cuda")
@@ -246,16 +258,29 @@ def run_gpu(args):
     launches = h.launches - launches0
     build_s = [a.elapsed_time(b) / 1e3 for a, b, _ in recs]
     step_s = [a.elapsed_time(c) / 1e3 for a, _, c in recs]
-    ny, ty_ms = h.profile_query("sigma_y_binomial")
+    ny, ty_ms = h.profile_query(ykern)
     n2, t2_ms = h.profile_query("sigma_gemm2")
     nw, tw_ms = h.profile_query("w_gemm")
     nt, tt_ms = h.profile_query("t_update")
     h.profile(False)
     resp_f, y_f, g2_f = work_flops(shape)
-    # per launch of the dominant kernel: its share of the Y-stage flops
-    y_per_launch = y_f * args.steps / max(ny, 1)
+    # per launch of the dominant kernel: its share of the Y-stage flops (on the
+    # tensor-core path the arithmetic is the 28 BF16 digit products)
+    y_per_launch = y_f * args.steps / max(ny, 1) * (DIGIT_PRODUCTS if tc else 1)
     y_avg_s = ty_ms / 1e3 / max(ny, 1)
     achieved = y_per_launch / y_avg_s / 1e9 if ny else None
+    peaks = measured_peaks()
+    if tc:
+        peak = peaks.get("bf16_tflops_sustained", 1700.0) * 1e3
+        roofline = {"kernel": ykern, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
+                    "frac": achieved / peak if achieved else None, "traffic": None,
+                    "fp64_equivalent_gflops": achieved / DIGIT_PRODUCTS if achieved else None,
+                    "peak_source": "bf16_tflops_sustained of measured (MEASURED_PEAKS.json)" if peaks
+                    else "sustained bf16 of fallback"}
+    else:
+        roofline = {"kernel": ykern, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS,
+                    "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS if achieved else None, "traffic": None,
+                    "peak_source": "nominal FP64 rate (profiling recipe table), of fallback"}
 
     # end to end through the C ABI with host buffers
     sh_h = torch.empty(sh.shape, dtype=torch.float64).pin_memory()
@@ -295,16 +320,13 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": total_step / builds * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "nocc": nocc, "nvir": nvir, "naux": naux,
-                       "nmom_max": shape.nmom_max, "screening": args.screening, "precision": "fp64",
+                       "nmom_max": shape.nmom_max, "screening": args.screening, "precision": args.precision,
                        "l2": "inputs larger than L2 (L is %.2f GB)" % (L.numel() * 8 / 1e9)},
             "stages_s": {"sigma_build": statistics.mean(build_s), "full_step": statistics.mean(step_s),
                          "w_gemm": tw_ms / 1e3 / args.steps, "t_update": tt_ms / 1e3 / args.steps,
-                         "sigma_y_binomial": ty_ms / 1e3 / args.steps, "sigma_gemm2": t2_ms / 1e3 / args.steps},
+                         ykern: ty_ms / 1e3 / args.steps, "sigma_gemm2": t2_ms / 1e3 / args.steps},
             "gflops_sigma_build": (resp_f + y_f + g2_f) / statistics.mean(build_s) / 1e9,
-            "roofline": {"kernel": "sigma_y_binomial", "bound": "alu", "achieved": achieved,
-                         "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                         "frac": achieved / FP64_PEAK_GFLOPS if achieved else None, "traffic": None,
-                         "peak_source": "nominal FP64 rate (profiling recipe table), of fallback"},
+            "roofline": roofline,
             "e2e": {"value": total_e2e / builds, "unit": "s",
                     "h2d_bytes_per_step": int(L_h.numel() * 8 + eps_h.numel() * 8),
                     "d2h_bytes_per_step": int(2 * sh.numel() * 8)},
@@ -330,6 +352,7 @@ def main():
     ap.add_argument("--impl", default="mgw", choices=["mgw", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(mgw_inputs.WORKLOADS))
     ap.add_argument("--screening", default="tda", choices=["tda", "rpa"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp64_tc"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

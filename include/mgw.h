@@ -49,8 +49,12 @@ typedef enum {
 
 typedef enum { MGW_TDA = 0, MGW_RPA = 1 } mgw_screening;
 
-/* Arithmetic of the bulk contractions.  FP64: float64 throughout. */
-typedef enum { MGW_FP64 = 0, MGW_BF16X3 = 1 } mgw_precision;
+/* Arithmetic of the bulk contractions.  FP64: float64 FMA units throughout.
+ * FP64_TC: the dominant contraction of the Sigma build on the BF16 tensor
+ * cores as an FP64-accurate digit-sliced product (see mgw_gemm_fp64_emu).
+ * BF16X3 is only the standalone mgw_gemm_bf16x3 product (FP32 accumulation
+ * is too coarse for the moment-to-Lanczos step, so no path uses it). */
+typedef enum { MGW_FP64 = 0, MGW_BF16X3 = 1, MGW_FP64_TC = 2 } mgw_precision;
 
 typedef struct mgw_handle mgw_handle;
 
@@ -188,6 +192,57 @@ mgw_status mgw_qp_solve(mgw_handle* h, const mgw_options* o,
                         double* E, double* weight, double* chi_phys,
                         double* eps_qp, double* rho,
                         double* mu_host, double* nelec_host, int* m_host);
+
+/*
+ * mgw_fsgw_step -- one outer iteration of Fock self-consistent GW
+ * (Algorithm 2, Sec. III F).  In the reference orbital basis of h and L:
+ *   1. L' = C^T L C; response moments, Sigma moments and both block-Lanczos
+ *      chains in the orbitals C with energies eps (o->screening, o->nquad);
+ *   2. the chains' coupling is carried to the reference basis (W~ = C W~');
+ *   3. zeta (the shift of d~ in Eq. 9) is chosen so that the Aufbau count of
+ *      Eq. 40 meets N = 2 nocc (golden section on [-1, 1] Ha), then F is made
+ *      consistent with the correlated density, F = h + J[rho] - K[rho]/2,
+ *      by a Pulay-DIIS Fock loop (space o->diis_space) at fixed zeta; the two
+ *      alternate until both hold (at most 20 rounds);
+ *   4. eps, C <- eigh(F), and the QP energies of Eq. 34 in that basis.
+ * Start from F = diag(eps_ref), C = I, eps = eps_ref, zeta = 0 for a
+ * canonical Hartree-Fock reference (h chosen so that F[rho_HF] = diag(eps)),
+ * or set init = 1 to have the step first take eps, C from eigh(F).
+ * Repeat until the moments and QP energies stop changing (o->conv_mom,
+ * o->conv_e); the convergence test is the caller's.
+ */
+typedef struct {
+  int nocc, nvir, naux, nmom_max; /* sizes; nmom_max <= 11 */
+  const double* h;        /* [nmo][nmo]        in   core Hamiltonian, reference basis */
+  const double* L;        /* [naux][nmo][nmo]  in   DF tensor, reference basis */
+  double* F;              /* [nmo][nmo]        in/out Fock matrix, reference basis */
+  double* C;              /* [nmo][nmo]        in/out orbitals (columns) of the last F */
+  double* eps;            /* [nmo]             in/out their energies */
+  double* eps_qp;         /* [nmo]             out  QP energies (Eq. 34) in the new orbitals */
+  double* sigma_ref;      /* [nmom][nmo][nmo]  out  Sigma(n,<) + Sigma(n,>) in the reference basis, or NULL */
+  double zeta;            /* host in/out */
+  double mu, nelec;       /* host out: chemical potential and Aufbau count at the end */
+  int inner_iters;        /* host out: Fock-loop iterations in this step */
+  int zeta_evals;         /* host out: H~ diagonalisations spent on zeta */
+  int init;               /* host in: 1 = derive eps, C from F first (cleared by the step) */
+} mgw_fsgw_state;
+
+mgw_status mgw_fsgw_step(mgw_handle* h, const mgw_options* o, mgw_fsgw_state* st);
+
+/*
+ * mgw_gemm_fp64_emu -- C = A B^T to FP64 accuracy on the BF16 tensor cores
+ * (tcgen05, TMA, TMEM).  Each row of A and B is scaled by a power of two and
+ * cut into 7 signed base-256 digits held exactly in BF16; the 28 digit
+ * products above 2^-64 of the leading term are integer GEMMs, accumulated
+ * exactly in FP32 over K chunks (1024 / (s + u - 1) wide) for the top 10
+ * and flushed into 64-bit integers, the rest in FP32 over all of K.  Error:
+ * a few units of 2^-53 times sum_k |A_ik| |B_jk|, as an FP64 GEMM.  Not in
+ * the paper; it is how the FP64 contractions of the path reach the tensor
+ * cores of a GPU whose FP64 units are few.
+ *   A [M][K], B [N][K] in (FP64, row-major);  C [M][N] out (FP64)
+ */
+mgw_status mgw_gemm_fp64_emu(mgw_handle* h, int M, int N, int K,
+                             const double* A, const double* B, double* C);
 
 /*
  * mgw_gemm_bf16x3 -- C = A B^T on the tensor cores (tcgen05, TMA, TMEM):

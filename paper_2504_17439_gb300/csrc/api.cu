@@ -35,6 +35,26 @@ mgw_status ws_reserve(mgw_handle* h, size_t bytes) {
   return MGW_OK;
 }
 
+mgw_status slot_buffer(mgw_handle* h, int id, size_t count, double** out) {
+  if ((int)h->slots.size() <= id) h->slots.resize(id + 1, {nullptr, 0});
+  auto& sl = h->slots[id];
+  const size_t bytes = count * sizeof(double);
+  if (sl.second < bytes) {
+    MGW_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (sl.first) MGW_CUDA(h, cudaFree(sl.first));
+    sl.first = nullptr;
+    sl.second = 0;
+    cudaError_t e = cudaMalloc(&sl.first, bytes);
+    if (e != cudaSuccess) {
+      sl.first = nullptr;
+      return fail(h, MGW_ERR_NOMEM, "slot buffer of %zu bytes: %s", bytes, cudaGetErrorString(e));
+    }
+    sl.second = bytes;
+  }
+  *out = static_cast<double*>(sl.first);
+  return MGW_OK;
+}
+
 mgw_status gemm_nn(mgw_handle* h, long M, long N, long K, double alpha, const double* A, long lda,
                    const double* B, long ldb, double beta, double* C, long ldc) {
   return dgemm<64, 64>(h, M, N, K, 1, ARowMajor{A, lda, 0}, BRowMajor{B, ldb, 0},
@@ -219,6 +239,8 @@ mgw_status mgw_destroy(mgw_handle* h) {
   if (!h) return MGW_OK;
   cudaStreamSynchronize(h->stream);
   clear_spans(h);
+  for (auto& sl : h->slots)
+    if (sl.first) cudaFree(sl.first);
   if (h->ws) cudaFree(h->ws);
   if (h->dinfo) cudaFree(h->dinfo);
   if (h->solver) cusolverDnDestroy(h->solver);

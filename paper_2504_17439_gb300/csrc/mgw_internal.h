@@ -20,6 +20,8 @@ struct mgw_handle {
   size_t ws_bytes = 0;
   int* dinfo = nullptr;      // device int for solver status words
   std::string err;
+  // buffers that persist across inner entry-point calls (which may move ws)
+  std::vector<std::pair<void*, size_t>> slots;
   // tracing: launches counted always; CUDA-event pairs per GEMM launch when enabled
   long launches = 0;
   bool prof = false;
@@ -55,6 +57,10 @@ mgw_status fail(mgw_handle* h, mgw_status s, const char* fmt, ...);
 
 // Ensure the handle's workspace holds at least `bytes`; grows (never shrinks).
 mgw_status ws_reserve(mgw_handle* h, size_t bytes);
+
+// A persistent device buffer of at least `count` doubles in slot `id` of the
+// handle (grows, never moves while large enough; freed by mgw_destroy).
+mgw_status slot_buffer(mgw_handle* h, int id, size_t count, double** out);
 
 // Bump allocator over the handle's workspace for the duration of one call.
 struct Arena {
@@ -162,19 +168,36 @@ struct is_tile_epi { static constexpr bool value = false; };
 template <class Epi>
 struct is_tile_epi<Epi, decltype(void(Epi::kTile))> { static constexpr bool value = Epi::kTile; };
 
+// Launch shape options of dgemm_kernel:
+//  tri    - M == N, symmetric result: blockIdx.x enumerates the upper-triangle
+//           tiles only (BM == BN) and the epilogue writes (m,n) and (n,m)
+//  kchunk - split K: blockIdx.z = batch + nbatch * split, split s covers
+//           k in [s*kchunk, (s+1)*kchunk); the epilogue gets the full z
+struct LaunchShape { int tri = 0; int nbatch = 1; long kchunk = 0; };
+
 template <int BM, int BN, class AOp, class BOp, class Epi>
 __global__ void __launch_bounds__(256)
-dgemm_kernel(long M, long N, long K, AOp A, BOp B, Epi epi) {
+dgemm_kernel(long M, long N, long K, AOp A, BOp B, Epi epi, LaunchShape ls) {
   constexpr int BK = 16, TM = BM / 16, TN = BN / 16;
   constexpr int LA = BM * BK / 256, LB = BN * BK / 256;
   constexpr int SA = BK * (BM + 1), SB = BK * (BN + 1);
   // [As0 | As1 | Bs0 | Bs1]; reused by tile epilogues after the K loop
   __shared__ double smem[2 * SA + 2 * SB];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const long m0 = (long)blockIdx.y * BM, n0 = (long)blockIdx.x * BN;
+  long tile_m = blockIdx.y, tile_n = blockIdx.x;
+  if (ls.tri) {  // upper-triangle tile t -> (row tile i, column tile j >= i)
+    long t = blockIdx.x, T = (N + BN - 1) / BN, i = 0;
+    while (t >= T - i) { t -= T - i; ++i; }
+    tile_m = i;
+    tile_n = i + t;
+  }
+  const long m0 = tile_m * BM, n0 = tile_n * BN;
   const int bz = blockIdx.z;
-  const double* Ab = A.base(bz);
-  const double* Bb = B.base(bz);
+  const int batch = bz % ls.nbatch;
+  const long kbeg = ls.kchunk > 0 ? (long)(bz / ls.nbatch) * ls.kchunk : 0;
+  const long kend = ls.kchunk > 0 ? (kbeg + ls.kchunk < K ? kbeg + ls.kchunk : K) : K;
+  const double* Ab = A.base(batch);
+  const double* Bb = B.base(batch);
   double acc[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
@@ -188,14 +211,14 @@ dgemm_kernel(long M, long N, long K, AOp A, BOp B, Epi epi) {
       int idx = tid + e * 256, mm, kk;
       if (AOp::kContig) { mm = idx / BK; kk = idx % BK; } else { kk = idx / BM; mm = idx % BM; }
       long m = m0 + mm, k = k0 + kk;
-      ra[e] = (m < M && k < K && A.ok(m, k)) ? __ldg(Ab + A.off(m, k)) : 0.0;
+      ra[e] = (m < M && k < kend && A.ok(m, k)) ? __ldg(Ab + A.off(m, k)) : 0.0;
     }
 #pragma unroll
     for (int e = 0; e < LB; ++e) {
       int idx = tid + e * 256, nn, kk;
       if (BOp::kContig) { nn = idx / BK; kk = idx % BK; } else { kk = idx / BN; nn = idx % BN; }
       long n = n0 + nn, k = k0 + kk;
-      rb[e] = (n < N && k < K) ? __ldg(Bb + B.off(k, n)) : 0.0;
+      rb[e] = (n < N && k < kend) ? __ldg(Bb + B.off(k, n)) : 0.0;
     }
   };
   auto sstore = [&](int buf) {
@@ -215,12 +238,12 @@ dgemm_kernel(long M, long N, long K, AOp A, BOp B, Epi epi) {
     }
   };
 
-  gload(0);
+  gload(kbeg);
   sstore(0);
   __syncthreads();
   int cur = 0;
-  for (long k0 = 0; k0 < K; k0 += BK) {
-    const bool more = k0 + BK < K;
+  for (long k0 = kbeg; k0 < kend; k0 += BK) {
+    const bool more = k0 + BK < kend;
     if (more) gload(k0 + BK);
     const double* As = smem + cur * SA;
     const double* Bs = smem + 2 * SA + cur * SB;
@@ -250,7 +273,14 @@ dgemm_kernel(long M, long N, long K, AOp A, BOp B, Epi epi) {
 #pragma unroll
       for (int j = 0; j < TN; ++j) {
         long n = n0 + tx + 16 * j;
-        if (n < N) epi(bz, m, n, acc[i][j]);
+        if (n >= N) continue;
+        if (ls.tri) {
+          if (m > n) continue;  // the (n, m) thread of a diagonal tile is the writer
+          epi(bz, m, n, acc[i][j]);
+          if (m != n) epi(bz, n, m, acc[i][j]);
+        } else {
+          epi(bz, m, n, acc[i][j]);
+        }
       }
     }
   }
@@ -258,16 +288,23 @@ dgemm_kernel(long M, long N, long K, AOp A, BOp B, Epi epi) {
 
 template <int BM, int BN, class AOp, class BOp, class Epi>
 mgw_status dgemm(mgw_handle* h, long M, long N, long K, int batch, const AOp& A, const BOp& B,
-                 const Epi& epi, const char* what) {
+                 const Epi& epi, const char* what, int tri = 0, int nsplit = 1) {
   if (M <= 0 || N <= 0 || batch <= 0) return MGW_OK;
-  dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM), (unsigned)batch);
+  LaunchShape ls;
+  ls.tri = tri;
+  ls.nbatch = batch;
+  if (nsplit > 1) ls.kchunk = ((K + nsplit - 1) / nsplit + 15) / 16 * 16;
+  const long splits = ls.kchunk > 0 ? (K + ls.kchunk - 1) / ls.kchunk : 1;
+  const long tn = (N + BN - 1) / BN, tm = (M + BM - 1) / BM;
+  dim3 grid(tri ? (unsigned)(tn * (tn + 1) / 2) : (unsigned)tn, tri ? 1u : (unsigned)tm,
+            (unsigned)(batch * splits));
   cudaEvent_t ea = nullptr, eb = nullptr;
   if (h->prof) {
     cudaEventCreate(&ea);
     cudaEventCreate(&eb);
     cudaEventRecord(ea, h->stream);
   }
-  dgemm_kernel<BM, BN, AOp, BOp, Epi><<<grid, 256, 0, h->stream>>>(M, N, K, A, B, epi);
+  dgemm_kernel<BM, BN, AOp, BOp, Epi><<<grid, 256, 0, h->stream>>>(M, N, K, A, B, epi, ls);
   mgw_status st = check_launch(h, what);
   if (h->prof) {
     cudaEventRecord(eb, h->stream);

@@ -16,8 +16,9 @@ namespace mgw {
 
 // W = T V^T : A = T [naux][ov] row-major, B(k=ia, n=Q) = V[Q][ia]
 static mgw_status w_gemm(mgw_handle* h, int naux, long ov, const double* T, const double* V, double* W) {
+  // W(t) is symmetric: upper-triangle tiles only, mirrored in the epilogue
   return dgemm<64, 64>(h, naux, naux, ov, 1, ARowMajor{T, ov, 0}, BNMajor{V, ov, 0},
-                       EpiStore{W, naux, 0, 1.0, 0.0}, "w_gemm");
+                       EpiStore{W, naux, 0, 1.0, 0.0}, "w_gemm", /*tri=*/1);
 }
 
 // T = T o d + alpha * W B : A = W [naux][naux], B = [naux][ov] row-major
@@ -169,7 +170,8 @@ extern "C" mgw_status mgw_response_moments(mgw_handle* h, const mgw_options* o, 
     return fail(h, MGW_ERR_ARG, "mgw_response_moments: unknown screening %d", o->screening);
   if (o->screening == MGW_RPA && (o->nquad < 2 || o->nquad % 2))
     return fail(h, MGW_ERR_ARG, "mgw_response_moments: nquad must be even and >= 2");
-  if (o->precision != MGW_FP64)
+  // the response recursion runs on the FP64 units under both FP64 modes
+  if (o->precision != MGW_FP64 && o->precision != MGW_FP64_TC)
     return fail(h, MGW_ERR_UNSUPPORTED, "mgw_response_moments: precision %d not built", o->precision);
   MGW_CUDA(h, cudaSetDevice(h->device));
   const long ov = (long)nocc * nvir;

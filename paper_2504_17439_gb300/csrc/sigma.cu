@@ -11,7 +11,15 @@
 //       Z(n)[P][(x,q)] = 2 sum_{t<=n} C(n,t) s^t eps_x^(n-t) Y(t)[P][(x,q)];
 //     Y never reaches HBM.
 //  2. GEMM2, batched over n:  Sigma(n)[p][q] += sum_{P,x} L[P][x][p] Z(n)[P][(x,q)].
+//
+// With precision MGW_FP64_TC the Y stage runs on the tensor cores as an
+// FP64-accurate digit-sliced GEMM (ozaki.h): W is sliced once in grouped-row
+// order (a 128-row tile holds all nmom orders of PB = 128/nmom aux rows), each
+// x-chunk of L is sliced as its transpose, and the same binomial weighting
+// runs in that kernel's epilogue from shared memory.
 #include "mgw_internal.h"
+#include "ozaki.h"
+#include "tc_gemm.h"
 
 #include <algorithm>
 #include <cmath>
@@ -22,6 +30,47 @@ constexpr int kMaxMom = 24;
 
 struct BinomCoef {
   double c[kMaxMom * (kMaxMom + 1) / 2];  // 2 C(n,t) s^t, row n at n(n+1)/2
+};
+
+// Binomial epilogue of the tensor-core Y stage.  Each of the 256 epilogue
+// threads holds 64 FP64 results of one tile row (t, pl); they are staged in
+// shared memory (the freed pipeline buffers) and recombined per (pl, column).
+struct EpiBinomialTC {
+  double* Z;
+  const double* eps;
+  int nmom, PB, naux, nmo;
+  long ncol;
+  BinomCoef bc;
+  __device__ void operator()(int row_local, int col_base, int m0, int n0, int, int N, const long long (&v)[64],
+                             double* smem) const {
+    constexpr int LD = 129;
+#pragma unroll
+    for (int j = 0; j < 64; ++j) smem[row_local * LD + col_base + j] = __longlong_as_double(v[j]);
+    tc::named_bar(1, 256);
+    const long g = m0 / 128;
+    const int tid = threadIdx.x - 64;
+    const int pairs = PB * 128;
+    for (int pi = tid; pi < pairs; pi += 256) {
+      const int pl = pi / 128, col = pi % 128;
+      const long P = g * PB + pl;
+      const long n = n0 + col;
+      if (P >= naux || n >= N) continue;
+      const double e = eps[n / nmo];
+      double y[kMaxMom], pe[kMaxMom];
+      pe[0] = 1.0;
+      for (int t = 0; t < nmom; ++t) {
+        y[t] = smem[(t * PB + pl) * LD + col];
+        if (t + 1 < nmom) pe[t + 1] = pe[t] * e;
+      }
+      for (int nn = 0; nn < nmom; ++nn) {
+        const double* cr = bc.c + nn * (nn + 1) / 2;
+        double z = 0.0;
+        for (int t = 0; t <= nn; ++t) z = fma(cr[t] * pe[nn - t], y[t], z);
+        Z[((long)nn * naux + P) * ncol + n] = z;
+      }
+    }
+  }
+  __device__ void abort() const { tc::named_bar(1, 256); }
 };
 
 // Tile epilogue of the Y stage: rows of the tile are (t, pl) with
@@ -78,6 +127,15 @@ struct EpiBinomial {
   }
 };
 
+// sig[i] = (accumulate ? sig[i] : 0) + sum_s part[s * count + i]
+__global__ void k_reduce_splits(long count, int nsplit, const double* part, double* sig, int accumulate) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x) {
+    double acc = accumulate ? sig[i] : 0.0;
+    for (int s = 0; s < nsplit; ++s) acc += part[(long)s * count + i];
+    sig[i] = acc;
+  }
+}
+
 }  // namespace mgw
 
 using namespace mgw;
@@ -92,8 +150,9 @@ extern "C" mgw_status mgw_sigma_moments(mgw_handle* h, const mgw_options* o, int
   if (nocc < 1 || nvir < 1 || naux < 1 || nmom < 1 || nmom > kMaxMom || !eps_G || !L || !Wmom || !sig_hole ||
       !sig_part)
     return fail(h, MGW_ERR_ARG, "mgw_sigma_moments: bad sizes or null pointer");
-  if (o->precision != MGW_FP64)
+  if (o->precision != MGW_FP64 && o->precision != MGW_FP64_TC)
     return fail(h, MGW_ERR_UNSUPPORTED, "mgw_sigma_moments: precision %d not built", o->precision);
+  const bool tc = o->precision == MGW_FP64_TC;
   MGW_CUDA(h, cudaSetDevice(h->device));
   const int nmo = nocc + nvir;
   constexpr int BM = 96, BN = 64;
@@ -105,10 +164,35 @@ extern "C" mgw_status mgw_sigma_moments(mgw_handle* h, const mgw_options* o, int
   int xc = o->xchunk > 0 ? o->xchunk : (int)std::max(1.0, std::floor((1024.0 * 1024 * 1024) / per_x));
   xc = std::min(xc, nmo);
 
+  // GEMM2 (symmetric output, upper tiles) is split along K until the launch
+  // has enough CTAs to fill the GPU several times over
+  const long tiles2 = ((nmo + 63) / 64) * ((nmo + 63) / 64 + 1) / 2;
+  int nsplit = (int)std::max(1L, std::min(16L, (152L * 8 + tiles2 * nmom - 1) / (tiles2 * nmom)));
+  const long n2 = (long)nmo * nmo;
+
+  // tensor-core Y stage: grouped W digits (once) and per-chunk L digits
+  const int PBt = std::max(1, 128 / nmom);
+  const long ngroups_t = (naux + PBt - 1) / PBt;
   Arena ar;
-  double* Z = nullptr;
+  double *Z = nullptr, *part = nullptr, *wdig = nullptr, *ldig = nullptr, *st = nullptr;
   ar.add(&Z, (size_t)nmom * naux * xc * nmo);
+  ar.add(&part, (size_t)nsplit * nmom * n2);
+  if (tc) {
+    ar.add(&wdig, oz::sliced_doubles(ngroups_t * 128, naux));
+    ar.add(&ldig, oz::sliced_doubles((long)xc * nmo, naux));
+    ar.add(&st, 1);
+  }
   MGW_TRY(ar.commit(h));
+  oz::Sliced sw, sl;
+  CUtensorMap mw;
+  int* dstatus = reinterpret_cast<int*>(st);
+  if (tc) {
+    if (nmom > 128) return fail(h, MGW_ERR_UNSUPPORTED, "mgw_sigma_moments: nmom > 128 on the tensor-core path");
+    MGW_CUDA(h, cudaMemsetAsync(dstatus, 0, sizeof(int), h->stream));
+    oz::place_sliced(wdig, ngroups_t * 128, naux, sw);
+    MGW_TRY(oz::slice_grouped(h, nmom, PBt, naux, Wmom, sw));
+    MGW_TRY(oz::digit_map(h, &mw, sw, oz::BM));
+  }
 
   for (int sector = 0; sector < 2; ++sector) {
     const int xbeg = sector == 0 ? 0 : nocc, xend = sector == 0 ? nocc : nmo;
@@ -127,18 +211,43 @@ extern "C" mgw_status mgw_sigma_moments(mgw_handle* h, const mgw_options* o, int
     for (int x0 = xbeg; x0 < xend; x0 += xc) {
       const int nx = std::min(xc, xend - x0);
       const long ncol = (long)nx * nmo;
-      EpiBinomial epi{Z, eps_G + x0, nmom, PB, naux, nmo, ncol, bc};
-      AGroupedMoments A{Wmom, nmom, PB, naux, BM};
-      BRowMajor B{L + (long)x0 * nmo, (long)nmo * nmo, 0};
-      MGW_TRY((dgemm<BM, BN>(h, ngroups * BM, ncol, naux, 1, A, B, epi, "sigma_y_binomial")));
+      if (tc) {
+        oz::place_sliced(ldig, ncol, naux, sl);
+        MGW_TRY(oz::slice_cols(h, ncol, naux, L + (long)x0 * nmo, (long)nmo * nmo, sl));
+        CUtensorMap ml;
+        MGW_TRY(oz::digit_map(h, &ml, sl, oz::BN));
+        EpiBinomialTC epi{Z, eps_G + x0, nmom, PBt, naux, nmo, ncol, bc};
+        MGW_TRY((oz::ozaki_launch(h, mw, ml, sw.exps, sl.exps, (int)(ngroups_t * 128), (int)ncol, naux,
+                                  oz::ARowsPlain{}, epi, dstatus, "sigma_y_binomial_tc")));
+      } else {
+        EpiBinomial epi{Z, eps_G + x0, nmom, PB, naux, nmo, ncol, bc};
+        AGroupedMoments A{Wmom, nmom, PB, naux, BM};
+        BRowMajor B{L + (long)x0 * nmo, (long)nmo * nmo, 0};
+        MGW_TRY((dgemm<BM, BN>(h, ngroups * BM, ncol, naux, 1, A, B, epi, "sigma_y_binomial")));
+      }
       // Sigma(n) (+)= sum_{P,x} L[P][x][p] Z(n)[(P,x)][q]
       AKMajor2 A2{L + (long)x0 * nmo, nx, (long)nmo * nmo, nmo, 0};
       BRowMajor B2{Z, nmo, (long)naux * ncol};
-      EpiStore e2{sig, nmo, (long)nmo * nmo, 1.0, first ? 0.0 : 1.0};
-      MGW_TRY((dgemm<64, 64>(h, nmo, nmo, (long)naux * nx, nmom, A2, B2, e2, "sigma_gemm2")));
+      const long K2 = (long)naux * nx;
+      const int ns = (int)std::min<long>(nsplit, std::max(1L, K2 / 256));
+      if (ns == 1) {
+        EpiStore e2{sig, nmo, n2, 1.0, first ? 0.0 : 1.0};
+        MGW_TRY((dgemm<64, 64>(h, nmo, nmo, K2, nmom, A2, B2, e2, "sigma_gemm2", /*tri=*/1)));
+      } else {
+        // partial sums per K split, z = n + nmom * split, then one reduction pass
+        EpiStore e2{part, nmo, n2, 1.0, 0.0};
+        MGW_TRY((dgemm<64, 64>(h, nmo, nmo, K2, nmom, A2, B2, e2, "sigma_gemm2", /*tri=*/1, ns)));
+        const long cnt = (long)nmom * n2;
+        const long kchunk = ((K2 + ns - 1) / ns + 15) / 16 * 16;
+        const int nsp = (int)((K2 + kchunk - 1) / kchunk);
+        k_reduce_splits<<<(unsigned)std::min<long>((cnt + 255) / 256, 152L * 16), 256, 0, h->stream>>>(
+            cnt, nsp, part, sig, first ? 0 : 1);
+        MGW_TRY(check_launch(h, "reduce_splits"));
+      }
       first = false;
     }
     if (first) MGW_CUDA(h, cudaMemsetAsync(sig, 0, sizeof(double) * nmom * nmo * nmo, h->stream));
   }
+  if (tc) return tc::check_tc_status(h, dstatus, "mgw_sigma_moments");
   return MGW_OK;
 }

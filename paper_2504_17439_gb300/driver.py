@@ -60,3 +60,39 @@ def evgw(h: mgw.Handle, eps: torch.Tensor, L: torch.Tensor, nocc: int, nmom_max:
         if max(dG, dW) < conv:
             return dict(eps_qp=e_new, iterations=it + 1, converged=True, history=hist)
     return dict(eps_qp=e_new, iterations=iters, converged=False, history=hist)
+
+
+def fsgw(h: mgw.Handle, hcore: torch.Tensor, L: torch.Tensor, eps: torch.Tensor, nocc: int, nmom_max: int,
+         screening: int = mgw.MGW_TDA, opts: mgw.Options | None = None, conv_e: float | None = None,
+         conv_mom: float | None = None, max_outer: int = 30, F0: torch.Tensor | None = None) -> dict:
+    """Fock self-consistency (Algorithm 2): mgw_fsgw_step until the
+    reference-basis moments and the QP energies stop changing."""
+    o = opts if opts is not None else mgw.options()
+    o.screening = screening
+    ce = o.conv_e if conv_e is None else conv_e
+    cm = o.conv_mom if conv_mom is None else conv_mom
+    naux, nmo = L.shape[0], L.shape[1]
+    nmom = 2 * nmom_max + 2
+    dev = L.device
+    # canonical reference: F = diag(eps), C = I; otherwise the first step takes
+    # the orbitals of F0 itself (init = 1)
+    F = torch.diag(eps).contiguous() if F0 is None else F0.clone().contiguous()
+    C = torch.eye(nmo, dtype=torch.float64, device=dev)
+    e = eps.clone()
+    eps_qp = torch.empty(nmo, dtype=torch.float64, device=dev)
+    sig = torch.empty((nmom, nmo, nmo), dtype=torch.float64, device=dev)
+    st = mgw.FsgwState(nocc, nmo - nocc, naux, nmom_max, hcore.data_ptr(), L.data_ptr(), F.data_ptr(),
+                       C.data_ptr(), e.data_ptr(), eps_qp.data_ptr(), sig.data_ptr(), 0.0, 0.0, 0.0, 0, 0,
+                       0 if F0 is None else 1)
+    prev_sig = prev_qp = None
+    hist = []
+    for outer in range(max_outer):
+        h.mgw_fsgw_step(o, st)
+        dsig = float((sig - prev_sig).abs().max()) if prev_sig is not None else float("inf")
+        dqp = float((eps_qp - prev_qp).abs().max()) if prev_qp is not None else float("inf")
+        hist.append(dict(outer=outer, inner=st.inner_iters, zeta=st.zeta, dsig=dsig, dqp=dqp, nelec=st.nelec,
+                         zeta_evals=st.zeta_evals))
+        prev_sig, prev_qp = sig.clone(), eps_qp.clone()
+        if dsig < cm and dqp < ce:
+            return dict(eps_qp=eps_qp, F=F, zeta=st.zeta, mu=st.mu, converged=True, history=hist)
+    return dict(eps_qp=eps_qp, F=F, zeta=st.zeta, mu=st.mu, converged=False, history=hist)

@@ -15,7 +15,7 @@ import torch
 from . import build as _build
 
 MGW_TDA, MGW_RPA = 0, 1
-MGW_FP64, MGW_BF16X3 = 0, 1
+MGW_FP64, MGW_BF16X3, MGW_FP64_TC = 0, 1, 2
 
 _STATUS = {
     0: "MGW_OK", -1: "MGW_ERR_ARG", -2: "MGW_ERR_CUDA", -3: "MGW_ERR_NOMEM", -4: "MGW_ERR_NOT_PD",
@@ -43,6 +43,16 @@ class Options(ctypes.Structure):
     ]
 
 
+class FsgwState(ctypes.Structure):
+    _fields_ = [
+        ("nocc", ctypes.c_int), ("nvir", ctypes.c_int), ("naux", ctypes.c_int), ("nmom_max", ctypes.c_int),
+        ("h", ctypes.c_void_p), ("L", ctypes.c_void_p), ("F", ctypes.c_void_p), ("C", ctypes.c_void_p),
+        ("eps", ctypes.c_void_p), ("eps_qp", ctypes.c_void_p), ("sigma_ref", ctypes.c_void_p),
+        ("zeta", ctypes.c_double), ("mu", ctypes.c_double), ("nelec", ctypes.c_double),
+        ("inner_iters", ctypes.c_int), ("zeta_evals", ctypes.c_int), ("init", ctypes.c_int),
+    ]
+
+
 _lib = None
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -52,6 +62,7 @@ _D = ctypes.c_double
 _SIGS = {
     "mgw_extract_ov": [_I, _I, _I, _P, _P],
     "mgw_gemm_bf16x3": [_I, _I, _I, _P, _P, _P],
+    "mgw_gemm_fp64_emu": [_I, _I, _I, _P, _P, _P],
     "mgw_response_moments": [_P, _I, _I, _I, _I, _P, _P, _P],
     "mgw_sigma_moments": [_P, _I, _I, _I, _I, _P, _P, _P, _P, _P],
     "mgw_block_lanczos": [_P, _I, _I, _P, _P, _P, _P, ctypes.POINTER(_I)],
@@ -91,6 +102,8 @@ def load(path: str | None = None):
     lib.mgw_profile_query.restype = _I
     lib.mgw_launch_count.argtypes = [_P]
     lib.mgw_launch_count.restype = ctypes.c_long
+    lib.mgw_fsgw_step.argtypes = [_P, _P, ctypes.POINTER(FsgwState)]
+    lib.mgw_fsgw_step.restype = _I
     for name, args in _SIGS.items():
         fn = getattr(lib, name)
         fn.argtypes = [_P] + args
@@ -175,6 +188,19 @@ class Handle:
             raise MgwError(st, (self._lib.mgw_last_error(self._h) or b"").decode())
 
     # -- the ABI entry points, same names ---------------------------------
+    def mgw_fsgw_step(self, opts: Options, st: FsgwState):
+        self._check(self._lib.mgw_fsgw_step(self._h, ctypes.byref(opts), ctypes.byref(st)))
+        return st
+
+    def mgw_gemm_fp64_emu(self, A, B, C=None):
+        """C = A B^T to FP64 accuracy on the tensor cores (exact BF16 digit products)."""
+        M, K = A.shape
+        N = B.shape[0]
+        C = C if C is not None else torch.empty((M, N), dtype=torch.float64, device=A.device)
+        self._check(self._lib.mgw_gemm_fp64_emu(self._h, M, N, K, _ptr(A, (M, K), "A"), _ptr(B, (N, K), "B"),
+                                                _ptr(C, (M, N), "C")))
+        return C
+
     def mgw_gemm_bf16x3(self, A, B, C=None):
         """C = A B^T on the tensor cores with BF16 hi/lo operand splits (3 products, FP32 accumulate)."""
         M, K = A.shape

@@ -23,15 +23,16 @@ def rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
-@pytest.fixture(scope="module")
-def run():
+@pytest.fixture(scope="module", params=["fp64", "fp64_tc"])
+def run(request):
     from paper_2504_17439_gb300 import build, driver, mgw
 
     build.build()
     shape, seed = mgw_inputs.workload("g0w0-nmo400-naux1600")
     eps, L = mgw_inputs.system(shape, seed)
     h = mgw.Handle(0)
-    r = driver.g0w0(h, torch.from_numpy(eps).cuda(), torch.from_numpy(L).cuda(), shape.nocc, shape.nmom_max)
+    o = mgw.options(precision=mgw.MGW_FP64 if request.param == "fp64" else mgw.MGW_FP64_TC)
+    r = driver.g0w0(h, torch.from_numpy(eps).cuda(), torch.from_numpy(L).cuda(), shape.nocc, shape.nmom_max, opts=o)
     out = {k: (v.cpu().numpy() if isinstance(v, torch.Tensor) else v) for k, v in r.items()
            if k not in ("hole", "part")}
     out["hole"] = tuple(x.cpu().numpy() if isinstance(x, torch.Tensor) else x for x in r["hole"])

@@ -30,3 +30,29 @@ def test_bf16x3_gemm_matches_fp64(h, M, N, K):
     scale = np.abs(A) @ np.abs(B).T
     err = np.abs(C - ref) / scale
     assert err.max() < 2e-5, err.max()
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (300, 520, 200), (1, 1, 1), (257, 17, 1000), (512, 384, 4800),
+                                   (130, 140, 2500)])
+def test_fp64_emulated_gemm_matches_fp64(h, M, N, K):
+    """Digit-sliced tensor-core GEMM: error within a few 2^-53 of sum_k |A||B|
+    (an FP64 GEMM's own bound), with a wide exponent spread across rows."""
+    g = np.random.default_rng(M * 5 + N * 11 + K)
+    A = g.standard_normal((M, K)) * np.exp2(g.integers(-20, 20, (M, 1)))
+    B = g.standard_normal((N, K)) * np.exp2(g.integers(-20, 20, (N, 1)))
+    A[:, :: max(1, K // 7)] *= 1e-9  # small entries inside a row
+    C = h.mgw_gemm_fp64_emu(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()).cpu().numpy()
+    ref = A @ B.T
+    scale = np.abs(A) @ np.abs(B).T
+    err = np.abs(C - ref) / scale
+    assert err.max() < 8 * 2.0**-52, err.max()
+
+
+def test_fp64_emulated_gemm_zero_rows(h):
+    A = np.zeros((130, 70))
+    B = np.random.default_rng(1).standard_normal((129, 70))
+    A[5] = 1.5
+    C = h.mgw_gemm_fp64_emu(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()).cpu().numpy()
+    ref = A @ B.T
+    assert np.abs(C - ref).max() <= 1e-15 * np.abs(ref).max()
+    assert np.all(C[np.arange(130) != 5] == 0)
