@@ -417,9 +417,14 @@ def evgw(eps, L, nocc, nmom_max, screening="tda", nq=48, g0=False, w0=False,
 #  F2  F[rho] = h + J[rho] - K[rho]/2 with rho the spin-summed correlated
 #      density of Eq. 40 (Tr rho = N), J_pq = sum_P L_Ppq sum_rs L_Prs rho_rs,
 #      K_pq = sum_P sum_rs L_Ppr rho_rs L_Psq.
-#  F3  zeta: golden-section search on [-1, 1] Ha of |N(zeta) - N| (the
-#      Aufbau count of Eq. 40 for H~(zeta)), at most 60 evaluations, stopping
-#      when the bracket is below 1e-8 Ha or the count is met to 1e-10.
+#  F3  zeta: the root of g(zeta) = N(zeta) - N (the Aufbau count of Eq. 40
+#      for H~(zeta)) nearest to the current zeta.  g has many roots (each
+#      change of the Aufbau filling shifts it), so the search scans outward
+#      from the current zeta in steps of 0.01 Ha for the nearest sign change,
+#      refines it by Illinois regula falsi (count met to 1e-10 or bracket
+#      below 1e-9 Ha, at most 60 evaluations), accepts it if |g| <= 1e-6
+#      (else it was a jump of the filling and the scan continues), and falls
+#      back to golden section on |g| over [-1, 1] Ha if no root is found.
 #  F4  Fock loop at fixed zeta: Pulay DIIS on F with error F[rho(F)] - F
 #      (space 12, Sec. IV B), plain iteration for the first two steps, until
 #      max |delta rho| < 1e-8 (at most 100 steps).
@@ -443,27 +448,69 @@ def rotate_df(L, C):
     return np.einsum("ap,Qab,bq->Qpq", C, L, C, optimize=True)
 
 
-def zeta_search(F, hole, part, nelec, lo=-1.0, hi=1.0, max_eval=60, tol=1e-8):
-    """Reading F3: golden section on |N(zeta) - N|."""
-    g = (math.sqrt(5.0) - 1.0) / 2.0
+def zeta_search(F, hole, part, nelec, start=0.0, step=0.01, lo=-1.0, hi=1.0, tol=1e-10, accept=1e-6):
+    """Reading F3.  Returns (zeta, |g(zeta)|, evaluations)."""
+    count = [0]
 
-    def f(z):
-        return abs(qp_solve(F, hole, part, nelec, z)["nelec"] - nelec)
+    def g(z):
+        count[0] += 1
+        return qp_solve(F, hole, part, nelec, z)["nelec"] - nelec
+
+    def refine(a, ga, b, gb):
+        # Illinois regula falsi on a bracket with ga * gb < 0
+        c, gc = (a, ga) if abs(ga) < abs(gb) else (b, gb)
+        for _ in range(60):
+            if abs(gc) <= tol or abs(b - a) < 1e-9:
+                break
+            c = b - gb * (b - a) / (gb - ga)
+            gc = g(c)
+            if gc * gb < 0:
+                a, ga = b, gb
+            else:
+                ga *= 0.5
+            b, gb = c, gc
+        return c, gc
+
+    z0 = min(max(start, lo), hi)
+    g0 = g(z0)
+    if abs(g0) <= tol:
+        return z0, abs(g0), count[0]
+    prev = {+1: (z0, g0), -1: (z0, g0)}
+    k = 1
+    while True:
+        moved = False
+        for side in (+1, -1):
+            z = z0 + side * k * step
+            if z < lo - 1e-12 or z > hi + 1e-12:
+                continue
+            moved = True
+            gz = g(z)
+            zp, gp = prev[side]
+            prev[side] = (z, gz)
+            if abs(gz) <= tol:
+                return z, abs(gz), count[0]
+            if gz * gp < 0:
+                c, gc = refine(zp, gp, z, gz)
+                if abs(gc) <= accept:
+                    return c, abs(gc), count[0]
+        if not moved:
+            break
+        k += 1
+    # fallback: golden section on |g| over [lo, hi]
+    r = (math.sqrt(5.0) - 1.0) / 2.0
     a, b = lo, hi
-    c, d = b - g * (b - a), a + g * (b - a)
-    fc, fd = f(c), f(d)
-    evals = 2
-    while b - a > tol and evals < max_eval and min(fc, fd) > 1e-10:
+    c, d = b - r * (b - a), a + r * (b - a)
+    fc, fd = abs(g(c)), abs(g(d))
+    while b - a > 1e-8 and count[0] < 200 and min(fc, fd) > tol:
         if fc <= fd:
             b, d, fd = d, c, fc
-            c = b - g * (b - a)
-            fc = f(c)
+            c = b - r * (b - a)
+            fc = abs(g(c))
         else:
             a, c, fc = c, d, fd
-            d = a + g * (b - a)
-            fd = f(d)
-        evals += 1
-    return (c, fc) if fc <= fd else (d, fd)
+            d = a + r * (b - a)
+            fd = abs(g(d))
+    return ((c, fc) if fc <= fd else (d, fd)) + (count[0],)
 
 
 def diis_extrapolate(Fs, errs):
@@ -525,7 +572,7 @@ def fsgw(h, L, eps, nocc, nmom_max, screening="tda", nq=48, max_outer=30, conv_e
         sig_ref = np.stack([C @ (a + b) @ C.T for a, b in zip(sh, sp)])
         inner = 0
         for rep in range(20):
-            zeta, nerr = zeta_search(F, hole_r, part_r, nelec)
+            zeta, nerr, _ = zeta_search(F, hole_r, part_r, nelec, start=zeta)
             F, rho, k = fock_loop(h, L, F, hole_r, part_r, nelec, zeta, diis_space)
             inner += k
             n_now = qp_solve(F, hole_r, part_r, nelec, zeta)["nelec"]
