@@ -259,9 +259,14 @@ def run_gpu(args):
     build_s = [a.elapsed_time(b) / 1e3 for a, b, _ in recs]
     step_s = [a.elapsed_time(c) / 1e3 for a, _, c in recs]
     ny, ty_ms = h.profile_query(ykern)
-    n2, t2_ms = h.profile_query("sigma_gemm2")
-    nw, tw_ms = h.profile_query("w_gemm")
-    nt, tt_ms = h.profile_query("t_update")
+
+    def both(name):  # FP64-unit and tensor-core variants of a stage
+        a, ta = h.profile_query(name)
+        b, tb = h.profile_query(name + "_tc")
+        return a + b, ta + tb
+    n2, t2_ms = both("sigma_gemm2")
+    nw, tw_ms = both("w_gemm")
+    nt, tt_ms = both("t_update")
     h.profile(False)
     resp_f, y_f, g2_f = work_flops(shape)
     # per launch of the dominant kernel: its share of the Y-stage flops (on the
@@ -340,6 +345,64 @@ def run_gpu(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+    h.close()
+    return 0
+
+
+def run_batched(args):
+    """Uneven batch (nmo ~ U{40..300}, nocc = round(nmo/6), naux = 4 nmo,
+    nmom_max 5, TDA): the grouped build of all systems vs one system at a time
+    through the single-system entry points; systems per second of each."""
+    import torch
+
+    from paper_2504_17439_gb300 import build, mgw
+
+    build.build()
+    shapes = mgw_inputs.batch_shapes(args.batched, seed=mgw_inputs.SEED_BASE + 300)
+    nmom = 12
+    systems = []
+    for i, sh in enumerate(shapes):
+        eps = mgw_inputs.orbital_energies(sh.nocc, sh.nvir, mgw_inputs.SEED_BASE + 300 + i)
+        L = mgw_inputs.df_tensor(sh.naux, sh.nmo, mgw_inputs.SEED_BASE + 300 + i)
+        systems.append(dict(nocc=sh.nocc, nvir=sh.nvir, naux=sh.naux, eps=torch.from_numpy(eps).cuda(),
+                            L=torch.from_numpy(L).cuda()))
+    h = mgw.Handle(0)
+    o = mgw.options()
+    stream = torch.cuda.current_stream()
+
+    def grouped():
+        return h.mgw_sigma_moments_batched(o, nmom, systems)
+
+    def sequential():
+        out = []
+        for sy in systems:
+            Lov = h.mgw_extract_ov(sy["nocc"], sy["nvir"], sy["L"])
+            W = h.mgw_response_moments(o, sy["nocc"], sy["nvir"], sy["naux"], nmom, sy["eps"], Lov)
+            out.append(h.mgw_sigma_moments(o, sy["nocc"], sy["nvir"], sy["naux"], nmom, sy["eps"], sy["L"], W))
+        return out
+
+    res = {}
+    for name, fn in (("grouped", grouped), ("sequential", sequential)):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            fn()
+        b.record(stream)
+        b.synchronize()
+        res[name] = a.elapsed_time(b) / 1e3 / args.steps
+    g, sq = grouped(), sequential()
+    diff = max(float((x[0] - y[0]).abs().max() / y[0].abs().max()) for x, y in zip(g, sq))
+    line = {"metric": "batched_sigma_build_systems_per_s", "value": len(systems) / res["grouped"], "unit": "systems/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "batch", "systems": len(systems),
+                                            "nmo": [s.nmo for s in shapes][:8] + ["..."], "nmom_max": 5},
+            "sequential_systems_per_s": len(systems) / res["sequential"],
+            "speedup_vs_sequential": res["sequential"] / res["grouped"],
+            "max_rel_diff_grouped_vs_sequential": diff}
+    print(json.dumps(line), flush=True)
     h.close()
     return 0
 

@@ -194,13 +194,38 @@ mgw_status mgw_qp_solve(mgw_handle* h, const mgw_options* o,
                         double* mu_host, double* nelec_host, int* m_host);
 
 /*
+ * mgw_sigma_moments_batched -- TDA response moments and Sigma(n,<),
+ * Sigma(n,>) of many independent systems of uneven size at once (the same
+ * quantities as mgw_response_moments + mgw_sigma_moments per system).  Each
+ * stage is one grouped launch over all systems: per moment order one launch
+ * for every W_s(t) and one for every update of eta~_s; per round of
+ * Green's-function index chunks one launch for every Y stage and one for
+ * every GEMM2 (a CTA finds its system and tile from a prefix sum of tile
+ * counts).  Not in the paper (which treats one molecule at a time).
+ *   sys: HOST array of nsys descriptors whose pointers are device pointers
+ *   1 <= nmom <= 24; o->screening must be MGW_TDA.
+ */
+typedef struct {
+  int nocc, nvir, naux;
+  const double* eps;      /* [nmo]              in */
+  const double* L;        /* [naux][nmo][nmo]   in */
+  double* sig_hole;       /* [nmom][nmo][nmo]   out */
+  double* sig_part;       /* [nmom][nmo][nmo]   out */
+} mgw_system;
+
+mgw_status mgw_sigma_moments_batched(mgw_handle* h, const mgw_options* o, int nsys, int nmom,
+                                     const mgw_system* sys);
+
+/*
  * mgw_fsgw_step -- one outer iteration of Fock self-consistent GW
  * (Algorithm 2, Sec. III F).  In the reference orbital basis of h and L:
  *   1. L' = C^T L C; response moments, Sigma moments and both block-Lanczos
  *      chains in the orbitals C with energies eps (o->screening, o->nquad);
  *   2. the chains' coupling is carried to the reference basis (W~ = C W~');
  *   3. zeta (the shift of d~ in Eq. 9) is chosen so that the Aufbau count of
- *      Eq. 40 meets N = 2 nocc (golden section on [-1, 1] Ha), then F is made
+ *      Eq. 40 meets N = 2 nocc (the root of N(zeta) - N nearest to the current
+ *      zeta: outward scan in 0.01 Ha steps, Illinois regula falsi; golden
+ *      section on |N(zeta) - N| over [-1, 1] Ha if no root), then F is made
  *      consistent with the correlated density, F = h + J[rho] - K[rho]/2,
  *      by a Pulay-DIIS Fock loop (space o->diis_space) at fixed zeta; the two
  *      alternate until both hold (at most 20 rounds);
@@ -225,9 +250,47 @@ typedef struct {
   int inner_iters;        /* host out: Fock-loop iterations in this step */
   int zeta_evals;         /* host out: H~ diagonalisations spent on zeta */
   int init;               /* host in: 1 = derive eps, C from F first (cleared by the step) */
+  /* learned warm start of the first zeta search of the step (not in the paper):
+   * a network of the mgw_mlp_* family with d_in = MGW_WS_FEATURES, d_out = 1
+   * predicts zeta - zeta_prev from ws_feat; NULL params = the plain search */
+  const float* ws_params;
+  const unsigned short* ws_wbf16;
+  int ws_width;
+  float ws_feat[8];       /* host out: the features of the first search */
+  double ws_target;       /* host out: zeta found by it minus zeta_prev (a training target) */
+  int ws_hit;             /* host out: 1 if the predicted bracket held the root */
 } mgw_fsgw_state;
 
+#define MGW_WS_FEATURES 8
+
 mgw_status mgw_fsgw_step(mgw_handle* h, const mgw_options* o, mgw_fsgw_state* st);
+
+/*
+ * Warm-start network (not in the paper): three dense layers with SiLU,
+ *   z1 = W1 x + b1, a1 = silu(z1); z2 = W2 a1 + b2, a2 = silu(z2); y = W3 a2 + b3.
+ * params: FP32 master vector [W1 | b1 | W2 | b2 | W3 | b3] (W row-major
+ * [out][in]); wbf16: the same layout in BF16, the copy every product reads.
+ * All device pointers; float32 data.
+ *  mgw_mlp_nparams   length of the packed vector
+ *  mgw_mlp_round     wbf16 = bf16(params)
+ *  mgw_mlp_forward   Y [batch][d_out] from X [batch][d_in]; acts (or NULL)
+ *                    receives z1, a1, z2, a2 ([4][batch][width]) for backward
+ *  mgw_mlp_backward  grad [nparams] of sum_b <dY_b, y_b> (BF16 rounding of the
+ *                    weights passed through as identity)
+ *  mgw_mlp_mse       dY = (Y - T)/batch, loss (device float) = |Y - T|^2 / (2 batch)
+ *  mgw_mlp_adam      one Adam step (beta 0.9, 0.999, eps 1e-8) on params,
+ *                    refreshing wbf16; step counts from 1
+ */
+long mgw_mlp_nparams(int d_in, int width, int d_out);
+mgw_status mgw_mlp_round(mgw_handle* h, long n, const float* params, unsigned short* wbf16);
+mgw_status mgw_mlp_forward(mgw_handle* h, int d_in, int width, int d_out, const float* params,
+                           const unsigned short* wbf16, int batch, const float* X, float* Y, float* acts);
+mgw_status mgw_mlp_backward(mgw_handle* h, int d_in, int width, int d_out, const unsigned short* wbf16,
+                            int batch, const float* X, const float* acts, const float* dY, float* grad);
+mgw_status mgw_mlp_mse(mgw_handle* h, int batch, int d_out, const float* Y, const float* T, float* dY,
+                       float* loss);
+mgw_status mgw_mlp_adam(mgw_handle* h, long n, float* params, unsigned short* wbf16, const float* grad,
+                        float* m, float* v, int step, float lr);
 
 /*
  * mgw_gemm_fp64_emu -- C = A B^T to FP64 accuracy on the BF16 tensor cores

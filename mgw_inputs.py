@@ -55,6 +55,8 @@ WORKLOADS = {
     "g0w0-nmo24-naux72": dict(shape=Shape(5, 19, 72, 5), seed=SEED_BASE + 0),
     # molecule-sized FP64 workload (TDA and RPA with a 48-node quadrature)
     "g0w0-nmo400-naux1600": dict(shape=Shape(60, 340, 1600, 7), seed=SEED_BASE + 100),
+    # mid-size system for profiler captures: inputs above L2, a few GB on device
+    "g0w0-nmo200-naux800": dict(shape=Shape(30, 170, 800, 7), seed=SEED_BASE + 300),
     # pigment-molecule scale, mixed-precision workload
     "g0w0-nmo1200-naux4800": dict(shape=Shape(240, 960, 4800, 7), seed=SEED_BASE + 200),
 }

@@ -8,8 +8,8 @@
 //     DIIS-accelerated Fock loop F <- F[rho] at fixed zeta, until both hold;
 //  4. eps, C <- eigh(F) and the QP energies (Eq. 34) in that eigenbasis.
 // Numerical choices (the paper gives the loops, not their numerics):
-// zeta by golden section on [-1, 1] Ha (<= 60 evaluations, bracket 1e-8 Ha or
-// count met to 1e-10); Pulay DIIS on F with error F[rho] - F, space
+// zeta as the root of N(zeta) - N nearest to the current zeta (outward scan
+// in 0.01 Ha steps, Illinois regula falsi, golden-section fallback); Pulay DIIS on F with error F[rho] - F, space
 // o->diis_space, plain steps first twice, until max |delta rho| < 1e-8
 // (<= 100 steps); at most 20 zeta/Fock rounds.
 #include "mgw_internal.h"
@@ -140,27 +140,86 @@ struct FsgwCtx {
     return MGW_OK;
   }
 
-  // golden section on |N(zeta) - N| over [-1, 1]
-  mgw_status zeta_search(const double* F, double* zeta, double* ferr, int* evals) {
-    const double g = (std::sqrt(5.0) - 1.0) / 2.0;
-    double a = -1.0, b = 1.0, c = b - g * (b - a), d = a + g * (b - a), fc, fd;
-    MGW_TRY(nerr(F, c, &fc));
-    MGW_TRY(nerr(F, d, &fd));
-    int ev = 2;
-    while (b - a > 1e-8 && ev < 60 && std::min(fc, fd) > 1e-10) {
+  // Illinois regula falsi on a bracket [a, b] with ga * gb < 0
+  mgw_status illinois(const double* F, double a, double ga, double b, double gb, double* zc, double* gcv,
+                      int* evals) {
+    double c = std::fabs(ga) < std::fabs(gb) ? a : b, gc = std::fabs(ga) < std::fabs(gb) ? ga : gb;
+    for (int it = 0; it < 60; ++it) {
+      if (std::fabs(gc) <= 1e-10 || std::fabs(b - a) < 1e-9) break;
+      c = b - gb * (b - a) / (gb - ga);
+      MGW_TRY(gval(F, c, &gc, evals));
+      if (gc * gb < 0) { a = b; ga = gb; } else { ga *= 0.5; }
+      b = c;
+      gb = gc;
+    }
+    *zc = c;
+    *gcv = gc;
+    return MGW_OK;
+  }
+
+  mgw_status gval(const double* F, double z, double* gz, int* evals) {  // g = N(z) - N
+    double ne = 0, mu = 0;
+    int m = 0;
+    MGW_TRY(qp(F, z, nullptr, &ne, &mu, &m));
+    *gz = ne - nelec;
+    ++*evals;
+    return MGW_OK;
+  }
+
+  // root of g(zeta) = N(zeta) - N nearest to *zeta: outward scan in steps of
+  // 0.01 Ha for a sign change, Illinois regula falsi on it (accepted when
+  // |g| <= 1e-6, else it was a jump of the filling and the scan goes on),
+  // golden section on |g| over [-1, 1] as the fallback
+  mgw_status zeta_search(const double* F, double* zeta, double* ferr, int* evals, const double* g_at_start = nullptr) {
+    const double lo = -1.0, hi = 1.0, step = 0.01, tol = 1e-10, accept = 1e-6;
+    const double z0 = std::min(std::max(*zeta, lo), hi);
+    double g0;
+    if (g_at_start && z0 == *zeta) g0 = *g_at_start;
+    else MGW_TRY(gval(F, z0, &g0, evals));
+    if (std::fabs(g0) <= tol) { *zeta = z0; *ferr = std::fabs(g0); return MGW_OK; }
+    double pz[2] = {z0, z0}, pg[2] = {g0, g0};
+    for (int k = 1;; ++k) {
+      bool moved = false;
+      for (int si = 0; si < 2; ++si) {
+        const double side = si == 0 ? 1.0 : -1.0;
+        const double z = z0 + side * k * step;
+        if (z < lo - 1e-12 || z > hi + 1e-12) continue;
+        moved = true;
+        double gz;
+        MGW_TRY(gval(F, z, &gz, evals));
+        const double zp = pz[si], gp = pg[si];
+        pz[si] = z;
+        pg[si] = gz;
+        if (std::fabs(gz) <= tol) { *zeta = z; *ferr = std::fabs(gz); return MGW_OK; }
+        if (gz * gp < 0) {
+          double c, gc;
+          MGW_TRY(illinois(F, zp, gp, z, gz, &c, &gc, evals));
+          if (std::fabs(gc) <= accept) { *zeta = c; *ferr = std::fabs(gc); return MGW_OK; }
+        }
+      }
+      if (!moved) break;
+    }
+    // fallback: golden section on |g| over [lo, hi]
+    const double r = (std::sqrt(5.0) - 1.0) / 2.0;
+    double a = lo, b = hi, c = b - r * (b - a), d = a + r * (b - a), fc, fd;
+    MGW_TRY(gval(F, c, &fc, evals));
+    MGW_TRY(gval(F, d, &fd, evals));
+    fc = std::fabs(fc);
+    fd = std::fabs(fd);
+    while (b - a > 1e-8 && *evals < 400 && std::min(fc, fd) > tol) {
       if (fc <= fd) {
         b = d; d = c; fd = fc;
-        c = b - g * (b - a);
-        MGW_TRY(nerr(F, c, &fc));
+        c = b - r * (b - a);
+        MGW_TRY(gval(F, c, &fc, evals));
+        fc = std::fabs(fc);
       } else {
         a = c; c = d; fc = fd;
-        d = a + g * (b - a);
-        MGW_TRY(nerr(F, d, &fd));
+        d = a + r * (b - a);
+        MGW_TRY(gval(F, d, &fd, evals));
+        fd = std::fabs(fd);
       }
-      ++ev;
     }
     if (fc <= fd) { *zeta = c; *ferr = fc; } else { *zeta = d; *ferr = fd; }
-    *evals += ev;
     return MGW_OK;
   }
 
@@ -332,9 +391,56 @@ extern "C" mgw_status mgw_fsgw_step(mgw_handle* h, const mgw_options* o, mgw_fsg
   // 3. zeta / Fock rounds
   int inner = 0, evals = 0;
   double zeta = st->zeta;
+  const double zeta_prev = zeta;
+  st->ws_hit = 0;
   for (int rep = 0; rep < 20; ++rep) {
     double ferr = 0;
-    MGW_TRY(cx.zeta_search(st->F, &zeta, &ferr, &evals));
+    if (rep == 0) {
+      // features of the first search: frontier energies of the current
+      // orbitals, the count error at the previous zeta, the occupation ratio
+      double fe[2];
+      MGW_CUDA(h, cudaMemcpyAsync(fe, st->eps + nocc - 1, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+      double g0;
+      MGW_TRY(cx.gval(st->F, zeta, &g0, &evals));  // synchronises
+      const float f[MGW_WS_FEATURES] = {(float)fe[0], (float)fe[1], (float)(fe[1] - fe[0]), (float)g0,
+                                        (float)(10.0 * g0), (float)zeta, (float)nocc / (float)nmo, 1.0f};
+      for (int i = 0; i < MGW_WS_FEATURES; ++i) st->ws_feat[i] = f[i];
+      bool done = false;
+      if (st->ws_params && st->ws_wbf16 && st->ws_width > 0) {
+        // prediction: zeta_hat = zeta_prev + y; bracket [zeta_prev, zeta_hat] or a
+        // narrow window around zeta_hat, else the plain search below
+        float* xy = reinterpret_cast<float*>(dots + 96);  // 8 inputs + 1 output
+        MGW_CUDA(h, cudaMemcpyAsync(xy, f, sizeof f, cudaMemcpyHostToDevice, h->stream));
+        MGW_TRY(mgw_mlp_forward(h, MGW_WS_FEATURES, st->ws_width, 1, st->ws_params, st->ws_wbf16, 1, xy, xy + 8,
+                                nullptr));
+        float y = 0.f;
+        MGW_CUDA(h, cudaMemcpyAsync(&y, xy + 8, sizeof y, cudaMemcpyDeviceToHost, h->stream));
+        MGW_CUDA(h, cudaStreamSynchronize(h->stream));
+        const double zh = std::min(1.0, std::max(-1.0, zeta + (double)y));
+        double gh;
+        MGW_TRY(cx.gval(st->F, zh, &gh, &evals));
+        double zc = zh, gc = gh;
+        if (std::fabs(gh) > 1e-10) {
+          double a = zeta, ga = g0;
+          if (gh * g0 >= 0) {  // same side: probe a little beyond the prediction
+            const double w = 2e-3 * (zh >= zeta ? 1.0 : -1.0);
+            a = std::min(1.0, std::max(-1.0, zh + w));
+            MGW_TRY(cx.gval(st->F, a, &ga, &evals));
+          }
+          if (ga * gh < 0) MGW_TRY(cx.illinois(st->F, a, ga, zh, gh, &zc, &gc, &evals));
+        }
+        if (std::fabs(gc) <= 1e-6) {
+          zeta = zc;
+          ferr = std::fabs(gc);
+          done = true;
+          st->ws_hit = 1;
+        }
+      }
+      if (!done) MGW_TRY(cx.zeta_search(st->F, &zeta, &ferr, &evals, &g0));
+      st->ws_target = zeta - zeta_prev;
+    } else {
+      MGW_TRY(cx.zeta_search(st->F, &zeta, &ferr, &evals));
+    }
     int k = 0;
     MGW_TRY(cx.fock_loop(st->F, zeta, dF, dE, space, &k));
     inner += k;

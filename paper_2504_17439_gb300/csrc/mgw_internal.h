@@ -175,27 +175,16 @@ struct is_tile_epi<Epi, decltype(void(Epi::kTile))> { static constexpr bool valu
 //           k in [s*kchunk, (s+1)*kchunk); the epilogue gets the full z
 struct LaunchShape { int tri = 0; int nbatch = 1; long kchunk = 0; };
 
+// One output tile: C(m0.., n0..) over k in [kbeg, kend), epilogue batch index bz.
 template <int BM, int BN, class AOp, class BOp, class Epi>
-__global__ void __launch_bounds__(256)
-dgemm_kernel(long M, long N, long K, AOp A, BOp B, Epi epi, LaunchShape ls) {
+__device__ __forceinline__ void dgemm_tile(long M, long N, long K, const AOp& A, const BOp& B, const Epi& epi,
+                                           long tile_m, long tile_n, int batch, int bz, long kbeg, long kend,
+                                           int tri, double* smem) {
   constexpr int BK = 16, TM = BM / 16, TN = BN / 16;
   constexpr int LA = BM * BK / 256, LB = BN * BK / 256;
   constexpr int SA = BK * (BM + 1), SB = BK * (BN + 1);
-  // [As0 | As1 | Bs0 | Bs1]; reused by tile epilogues after the K loop
-  __shared__ double smem[2 * SA + 2 * SB];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  long tile_m = blockIdx.y, tile_n = blockIdx.x;
-  if (ls.tri) {  // upper-triangle tile t -> (row tile i, column tile j >= i)
-    long t = blockIdx.x, T = (N + BN - 1) / BN, i = 0;
-    while (t >= T - i) { t -= T - i; ++i; }
-    tile_m = i;
-    tile_n = i + t;
-  }
   const long m0 = tile_m * BM, n0 = tile_n * BN;
-  const int bz = blockIdx.z;
-  const int batch = bz % ls.nbatch;
-  const long kbeg = ls.kchunk > 0 ? (long)(bz / ls.nbatch) * ls.kchunk : 0;
-  const long kend = ls.kchunk > 0 ? (kbeg + ls.kchunk < K ? kbeg + ls.kchunk : K) : K;
   const double* Ab = A.base(batch);
   const double* Bb = B.base(batch);
   double acc[TM][TN];
@@ -274,7 +263,7 @@ dgemm_kernel(long M, long N, long K, AOp A, BOp B, Epi epi, LaunchShape ls) {
       for (int j = 0; j < TN; ++j) {
         long n = n0 + tx + 16 * j;
         if (n >= N) continue;
-        if (ls.tri) {
+        if (tri) {
           if (m > n) continue;  // the (n, m) thread of a diagonal tile is the writer
           epi(bz, m, n, acc[i][j]);
           if (m != n) epi(bz, n, m, acc[i][j]);
@@ -284,6 +273,59 @@ dgemm_kernel(long M, long N, long K, AOp A, BOp B, Epi epi, LaunchShape ls) {
       }
     }
   }
+}
+
+template <int BM, int BN>
+struct DgemmSmem { static constexpr int kDoubles = 2 * 16 * (BM + 1) + 2 * 16 * (BN + 1); };
+
+__device__ __forceinline__ void tri_tile(long t, long T, long& i, long& j) {
+  i = 0;
+  while (t >= T - i) { t -= T - i; ++i; }
+  j = i + t;
+}
+
+template <int BM, int BN, class AOp, class BOp, class Epi>
+__global__ void __launch_bounds__(256)
+dgemm_kernel(long M, long N, long K, AOp A, BOp B, Epi epi, LaunchShape ls) {
+  __shared__ double smem[DgemmSmem<BM, BN>::kDoubles];
+  long tile_m = blockIdx.y, tile_n = blockIdx.x;
+  if (ls.tri) tri_tile(blockIdx.x, (N + BN - 1) / BN, tile_m, tile_n);
+  const int bz = blockIdx.z;
+  const int batch = bz % ls.nbatch;
+  const long kbeg = ls.kchunk > 0 ? (long)(bz / ls.nbatch) * ls.kchunk : 0;
+  const long kend = ls.kchunk > 0 ? (kbeg + ls.kchunk < K ? kbeg + ls.kchunk : K) : K;
+  dgemm_tile<BM, BN>(M, N, K, A, B, epi, tile_m, tile_n, batch, bz, kbeg, kend, ls.tri, smem);
+}
+
+// Grouped GEMM: one launch over many independent problems of different
+// shapes.  tile_start[p] is the first linear tile of problem p (prefix sum,
+// tile_start[nprob] = total); a CTA finds its problem by binary search.
+template <class AOp, class BOp, class Epi>
+struct GroupItem {
+  long M, N, K;
+  AOp A;
+  BOp B;
+  Epi epi;
+  int tri;
+};
+
+template <int BM, int BN, class AOp, class BOp, class Epi>
+__global__ void __launch_bounds__(256)
+dgemm_grouped_kernel(const GroupItem<AOp, BOp, Epi>* items, const long* tile_start, int nprob) {
+  __shared__ double smem[DgemmSmem<BM, BN>::kDoubles];
+  const long t = blockIdx.x;
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tile_start[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  const GroupItem<AOp, BOp, Epi> it = items[lo];
+  const long local = t - tile_start[lo];
+  const long tn = (it.N + BN - 1) / BN;
+  long tile_m, tile_n;
+  if (it.tri) tri_tile(local, tn, tile_m, tile_n);
+  else { tile_m = local / tn; tile_n = local % tn; }
+  dgemm_tile<BM, BN>(it.M, it.N, it.K, it.A, it.B, it.epi, tile_m, tile_n, 0, 0, 0, it.K, it.tri, smem);
 }
 
 template <int BM, int BN, class AOp, class BOp, class Epi>

@@ -122,6 +122,56 @@ mgw_status slice_cols(mgw_handle* h, long rows, long K, const double* X, long ld
   return check_launch(h, "slice_cols");
 }
 
+// 32 result rows per CTA (256 threads); element (r, k) = X[roff(r) + koff(k)]
+__global__ void k_slice_gather(long rows, long K, const double* __restrict__ X, Gather g, __nv_bfloat16* dig,
+                               long ld, int* exps) {
+  __shared__ double smax[8][32];
+  __shared__ int sexp[32];
+  __shared__ __nv_bfloat16 sd[kSlices][32][65];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long r0 = (long)blockIdx.x * 32;
+  const long r = r0 + lane;
+  const long ro = r < rows ? (r / g.rdiv) * g.rhi + (r % g.rdiv) * g.rlo : 0;
+  double mx = 0.0;
+  if (r < rows)
+    for (long k = w; k < K; k += 8) mx = fmax(mx, fabs(X[ro + (k / g.kdiv) * g.khi + (k % g.kdiv) * g.klo]));
+  smax[w][lane] = mx;
+  __syncthreads();
+  if (w == 0) {
+    double m = smax[0][lane];
+    for (int i = 1; i < 8; ++i) m = fmax(m, smax[i][lane]);
+    const int e = row_exponent(m);
+    sexp[lane] = e;
+    if (r < rows) exps[r] = e;
+  }
+  __syncthreads();
+  const int e = sexp[lane];
+  const long plane = rows * ld;
+  for (long k0 = 0; k0 < ld; k0 += 64) {
+    for (int kk = w; kk < 64; kk += 8) {
+      const long k = k0 + kk;
+      const double x = (r < rows && k < K) ? X[ro + (k / g.kdiv) * g.khi + (k % g.kdiv) * g.klo] : 0.0;
+      __nv_bfloat16 d[kSlices];
+      digits_of(x, e, d);
+#pragma unroll
+      for (int s = 0; s < kSlices; ++s) sd[s][lane][kk] = d[s];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kSlices * 32 * 64; i += 256) {
+      const int s = i / (32 * 64), rr = (i / 64) % 32, kk = i % 64;
+      const long k = k0 + kk;
+      if (r0 + rr < rows && k < ld) dig[s * plane + (r0 + rr) * ld + k] = sd[s][rr][kk];
+    }
+    __syncthreads();
+  }
+}
+
+mgw_status slice_gather(mgw_handle* h, long rows, long K, const double* X, const Gather& g, Sliced& out) {
+  k_slice_gather<<<(unsigned)((rows + 31) / 32), 256, 0, h->stream>>>(
+      rows, K, X, g, static_cast<__nv_bfloat16*>(out.digits), out.ld, out.exps);
+  return check_launch(h, "slice_gather");
+}
+
 mgw_status digit_map(mgw_handle* h, CUtensorMap* map, const Sliced& s, int box_rows) {
   return tc::make_map_3d(h, map, s.digits, s.ld, s.rows, kSlices, s.ld * 2, s.rows * s.ld * 2, box_rows, 1);
 }
@@ -135,12 +185,12 @@ size_t sliced_doubles(long rows, long K) {
 struct EpiStoreRows {
   double* C;
   long ldc;
-  __device__ void operator()(int row_local, int col_base, int m0, int n0, int M, int N, const long long (&v)[64],
-                             double*) const {
+  __device__ void operator()(int row_local, int col_base, int m0, int n0, int M, int N,
+                             const long long (&v)[kCols], double*) const {
     const int row = m0 + row_local;
     if (row >= M) return;
 #pragma unroll
-    for (int j = 0; j < 64; ++j) {
+    for (int j = 0; j < kCols; ++j) {
       const int col = n0 + col_base + j;
       if (col < N) C[(long)row * ldc + col] = __longlong_as_double(v[j]);
     }

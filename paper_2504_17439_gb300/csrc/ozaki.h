@@ -9,19 +9,26 @@
 // and every digit product is an integer GEMM that the tensor core
 // accumulates EXACTLY in FP32 as long as the running sum stays below 2^24:
 // for level l = s + u (l - 1 products) that holds for K chunks of at most
-// 1024 / (l - 1).  Levels 2..5 (the top 10 products) are accumulated exactly
-// chunk by chunk and flushed into a 64-bit integer per element (registers of
-// the epilogue warps); levels 6..S+1 sit below 2^-48 of the top and are
-// accumulated in FP32 over the whole K, where their rounding is negligible.
-// With S = 7 (28 products) the result carries about 53 bits.
+// 1024 / (l - 1).  Levels 2..7 (the top 21 products) are accumulated exactly
+// chunk by chunk and flushed into 64-bit integers per element: levels 2..5
+// into registers of the epilogue warps, levels 6..7 into the spare half of
+// TMEM.  Level S+1 = 8 (7 products, below 2^-56 of the top) accumulates in
+// FP32 over the whole K: the tensor core truncates as it accumulates, and
+// only this deepest level can afford that.  With S = 7 (28 products) the
+// result carries about 53 bits.
 //
-// CTA: 128 x 128 output tile, 320 threads:
+// CTA: 128 x 96 output tile, 320 threads:
 //   warp 0     TMA producer (digit tiles of A and B, 3D maps: k, row, digit)
-//   warp 1     TMEM allocation (2 x 128 columns) and the MMA issuer
+//   warp 1     TMEM allocation (512 columns) and the MMA issuer
 //   warps 2-9  epilogue: warp w reads TMEM lanes 32 (w % 4).., columns
-//              64 ((w - 2) / 4)..; each thread owns 64 elements of one row
-// The two TMEM accumulators alternate between phases so the flush of one
-// overlaps the MMAs of the next.  All waits are time-bounded.
+//              48 ((w - 2) / 4)..; each thread owns 48 elements of one row
+// TMEM (512 columns): two FP32 accumulators [0,96) and [96,192) alternate
+// between phases so the flush of one overlaps the MMAs of the next; columns
+// [192,384) hold the level-6..7 integer accumulator (two words per element).
+// The tile is 96 wide so that the levels-2..5 integers (48 x int64 per
+// thread) fit the register budget of a 320-thread block: ten warps put three
+// on one SM sub-partition, whose 16K registers then allow 168 per thread.
+// All waits are time-bounded.
 #pragma once
 
 #include "tc_common.h"
@@ -30,13 +37,16 @@
 namespace mgw {
 namespace oz {
 
-constexpr int BM = 128, BN = 128, BK = 64;
+constexpr int BM = 128, BN = 96, BK = 64;
+constexpr int kCols = BN / 2;          // output columns per epilogue thread
 constexpr int kSlices = 7;
-constexpr int kExactTop = 5;          // levels 2..5 accumulated exactly
+constexpr int kExactTop = 7;          // levels 2..7 accumulated exactly
+constexpr int kRegTop = 5;            // levels 2..5 in registers, 6..7 in TMEM
 constexpr int kThreads = 320;
-constexpr int kStages = 6;
-constexpr int kTileBytes = BM * BK * 2;  // one A or B digit tile (16 KB)
-constexpr int kStageBytes = 2 * kTileBytes;
+constexpr int kStages = 7;
+constexpr int kTileBytes = BM * BK * 2;  // one A digit tile (16 KB)
+constexpr int kTileBytesB = BN * BK * 2; // one B digit tile (12 KB)
+constexpr int kStageBytes = kTileBytes + kTileBytesB;
 constexpr int kSmemBytes = 1024 + kStages * kStageBytes + 256;
 constexpr uint64_t kWaitNs = 2000000000ull;
 
@@ -129,7 +139,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
     fence_barrier_init();
   }
   if (warp == 1) {
-    tmem_alloc(tmem_slot, 256);
+    tmem_alloc(tmem_slot, 512);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -194,12 +204,21 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
     // ---------------- epilogue warps 2..9
     const int quad = warp & 3, half = (warp - 2) >> 2;
     const int row_local = quad * 32 + lane;
-    const int col_base = half * 64;
-    long long acc[64];
+    const int col_base = half * kCols;
+    long long acc[kCols];
 #pragma unroll
-    for (int j = 0; j < 64; ++j) acc[j] = 0;
+    for (int j = 0; j < kCols; ++j) acc[j] = 0;
     const int row = m0 + row_local;
     const int ei = row < M ? ea[row] : 0;
+    // this thread's 48 elements of the level-6..7 integer accumulator: 96 words
+    const uint32_t tw = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(2 * BN) + (uint32_t)(2 * col_base);
+    {
+      uint32_t z[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) z[j] = 0u;
+#pragma unroll
+      for (int c = 0; c < kCols / 8; ++c) tmem_st16u(tw + 16 * c, z);
+    }
     bool ok = true;
     const int nph = sched.phases();
     int l_of_phase = 2, chunk_idx = 0;
@@ -216,30 +235,55 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
       if (!is_low) {
         // level of this phase, walking the same chunking as Schedule
         const int l = l_of_phase;
-        const float up = (float)(1 << (8 * (l - 2)));   // v * 2^8(l-2) is an integer
-        const int shift = 8 * (kExactTop - l);
+        if (l <= kRegTop) {
+          const float up = (float)(1 << (8 * (l - 2)));   // v * 2^8(l-2) is an integer
+          const int shift = 8 * (kRegTop - l);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          float v[16];
-          tmem_ld16(ta + c * 16, v);
+          for (int c = 0; c < kCols / 16; ++c) {
+            float v[16];
+            tmem_ld16(ta + c * 16, v);
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-            acc[c * 16 + j] += (long long)__float2int_rn(v[j] * up) << shift;
+            for (int j = 0; j < 16; ++j)
+              acc[c * 16 + j] += (long long)__float2int_rn(v[j] * up) << shift;
+          }
+        } else {
+          // levels 6..7 in units of 2^-40 (d~ units): I_l = v 2^8(l-2), scaled by 2^8(7-l)
+          const float up = l == 6 ? 0x1p32f : 0x1p40f;
+          const int shift = 8 * (kExactTop - l);
+#pragma unroll 1
+          for (int c = 0; c < kCols / 8; ++c) {  // 8 elements (16 words) at a time
+            float v[16];
+            tmem_ld16(ta + (c >> 1) * 16, v);
+            uint32_t w[16];
+            tmem_ld16u(tw + 16 * c, w);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              long long t = (long long)(((unsigned long long)w[2 * j + 1] << 32) | w[2 * j]);
+              t += (long long)__float2int_rn(v[(c & 1) * 8 + j] * up) << shift;
+              w[2 * j] = (uint32_t)(unsigned long long)t;
+              w[2 * j + 1] = (uint32_t)((unsigned long long)t >> 32);
+            }
+            tmem_st16u(tw + 16 * c, w);
+          }
         }
         const int nchunks = (sched.kb_total + chunk_of_level(l) / BK - 1) / (chunk_of_level(l) / BK);
         if (++chunk_idx == nchunks) { chunk_idx = 0; ++l_of_phase; }
       } else {
-        // last phase: value = 2^(e_i + f_j - 16) (acc 2^-24 + low), kept in acc's registers
+        // last phase: value = 2^(e_i + f_j - 16) (acc 2^-24 + acc67 2^-40 + low), kept in acc's registers
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 0; c < kCols / 8; ++c) {
           float v[16];
-          tmem_ld16(ta + c * 16, v);
+          tmem_ld16(ta + (c >> 1) * 16, v);
+          uint32_t w[16];
+          tmem_ld16u(tw + 16 * c, w);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int col = n0 + col_base + c * 16 + j;
+          for (int j = 0; j < 8; ++j) {
+            const int e = c * 8 + j;
+            const int col = n0 + col_base + e;
             const int fj = col < N ? eb[col] : 0;
-            acc[c * 16 + j] =
-                __double_as_longlong(ldexp((double)acc[c * 16 + j] * 0x1p-24 + (double)v[j], ei + fj - 16));
+            const long long a67 = (long long)(((unsigned long long)w[2 * j + 1] << 32) | w[2 * j]);
+            acc[e] = __double_as_longlong(
+                ldexp((double)acc[e] * 0x1p-24 + (double)a67 * 0x1p-40 + (double)v[(c & 1) * 8 + j], ei + fj - 16));
           }
         }
       }
@@ -257,7 +301,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem, 256);
+    tmem_dealloc(tmem, 512);
   }
 }
 
@@ -276,6 +320,11 @@ mgw_status slice_rows(mgw_handle* h, long rows, long K, const double* X, long ld
 mgw_status slice_grouped(mgw_handle* h, int nmom, int PB, int naux, const double* W, Sliced& out);
 // slice the transpose: rows r of the result are columns of X: Y[r][k] = X[k * ldx + r]
 mgw_status slice_cols(mgw_handle* h, long rows, long K, const double* X, long ldx, Sliced& out);
+// slice a gathered matrix: element (r, k) = X[roff(r) + koff(k)] with
+// roff(r) = (r / rdiv) rhi + (r % rdiv) rlo, koff(k) = (k / kdiv) khi + (k % kdiv) klo;
+// CTAs take 32 consecutive rows, so rlo = 1 keeps the reads coalesced
+struct Gather { long rdiv, rhi, rlo, kdiv, khi, klo; };
+mgw_status slice_gather(mgw_handle* h, long rows, long K, const double* X, const Gather& g, Sliced& out);
 size_t sliced_doubles(long rows, long K);           // workspace for rows x K digits + exponents
 void place_sliced(double* mem, long rows, long K, Sliced& s);
 // 3D tensor map over digits: (k, row, digit), box (64, box_rows, 1)
@@ -306,6 +355,52 @@ mgw_status ozaki_launch(mgw_handle* h, const CUtensorMap& mA, const CUtensorMap&
   }
   return st;
 }
+
+}  // namespace oz
+}  // namespace mgw
+
+namespace mgw {
+namespace oz {
+
+// Per-element epilogue adaptor: f(row, col, value) for every in-range element.
+template <class F>
+struct EpiElem {
+  F f;
+  __device__ void operator()(int row_local, int col_base, int m0, int n0, int M, int N,
+                             const long long (&v)[kCols], double*) const {
+    const int row = m0 + row_local;
+    if (row >= M) return;
+#pragma unroll 4
+    for (int j = 0; j < kCols; ++j) {
+      const int col = n0 + col_base + j;
+      if (col < N) f(row, col, __longlong_as_double(v[j]));
+    }
+  }
+  __device__ void abort() const {}
+};
+
+struct FStore {  // C[row][col] = alpha v + beta C
+  double* C; long ldc; double alpha, beta;
+  __device__ void operator()(int r, int c, double v) const {
+    double* q = C + (long)r * ldc + c;
+    *q = beta == 0.0 ? alpha * v : alpha * v + beta * *q;
+  }
+};
+struct FDiagUpdate {  // T[row][col] = T d[col] + alpha v
+  double* T; long ldt; const double* d; double alpha;
+  __device__ void operator()(int r, int c, double v) const {
+    double* q = T + (long)r * ldt + c;
+    *q = *q * d[c] + alpha * v;
+  }
+};
+struct FSigmaN {  // column (n, q): Sigma(n)[row][q] (+)= v
+  double* sig; int nmo; double beta;
+  __device__ void operator()(int r, int c, double v) const {
+    const int n = c / nmo, q = c % nmo;
+    double* p = sig + ((long)n * nmo + r) * nmo + q;
+    *p = beta == 0.0 ? v : v + *p;
+  }
+};
 
 }  // namespace oz
 }  // namespace mgw

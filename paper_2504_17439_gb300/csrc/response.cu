@@ -7,7 +7,15 @@
 // columns ia by D_ia.  Each order is two GEMMs: W(n) (naux x naux, K = ov)
 // and the update, whose epilogue applies the diagonal term in place, so T
 // is read and written once per order and no intermediate is stored.
+//
+// With precision MGW_FP64_TC (TDA) both GEMMs of an order run as
+// FP64-accurate digit-sliced products on the tensor cores (ozaki.h): V is
+// sliced once as rows (for W = T V^T) and once transposed (for W V), T and
+// W(t) are sliced before each use, and the update's epilogue applies
+// T o D + 2 acc exactly as the FP64 kernel does.
 #include "mgw_internal.h"
+#include "ozaki.h"
+#include "tc_gemm.h"
 
 #include <cmath>
 #include <vector>
@@ -178,11 +186,20 @@ extern "C" mgw_status mgw_response_moments(mgw_handle* h, const mgw_options* o, 
   const long na2 = (long)naux * naux;
   const long tsz = (long)naux * ov;
 
+  const bool use_tc = o->screening == MGW_TDA && o->precision == MGW_FP64_TC;
   Arena ar;
   double *D = nullptr, *T0 = nullptr, *T1 = nullptr, *aux = nullptr, *work = nullptr, *mm = nullptr;
+  double *vd = nullptr, *vtd = nullptr, *td = nullptr, *wd = nullptr, *st = nullptr;
   ar.add(&D, ov);
   ar.add(&T0, tsz);
   ar.add(&mm, 2);
+  if (use_tc) {  // digit planes: V (rows Q, K = ov), V^T (rows ia, K = naux), T and W(t) per order
+    ar.add(&vd, oz::sliced_doubles(naux, ov));
+    ar.add(&vtd, oz::sliced_doubles(ov, naux));
+    ar.add(&td, oz::sliced_doubles(naux, ov));
+    ar.add(&wd, oz::sliced_doubles(naux, naux));
+    ar.add(&st, 1);
+  }
   if (o->screening == MGW_RPA) {
     ar.add(&T1, tsz);
     ar.add(&aux, tsz + 2 * ov);  // V o D, D^2, spare
@@ -190,6 +207,37 @@ extern "C" mgw_status mgw_response_moments(mgw_handle* h, const mgw_options* o, 
   }
   MGW_TRY(ar.commit(h));
   MGW_TRY(energy_differences(h, nocc, nvir, eps_W, D));
+
+  if (use_tc) {
+    int* dstatus = reinterpret_cast<int*>(st);
+    MGW_CUDA(h, cudaMemsetAsync(dstatus, 0, sizeof(int), h->stream));
+    oz::Sliced sv, svt, stt, sww;
+    oz::place_sliced(vd, naux, ov, sv);
+    oz::place_sliced(vtd, ov, naux, svt);
+    oz::place_sliced(td, naux, ov, stt);
+    oz::place_sliced(wd, naux, naux, sww);
+    MGW_TRY(oz::slice_rows(h, naux, ov, Lov, ov, sv));
+    MGW_TRY(oz::slice_gather(h, ov, naux, Lov, oz::Gather{ov + 1, 0, 1, naux + 1, 0, ov}, svt));
+    CUtensorMap mv, mvt, mt, mw;
+    MGW_TRY(oz::digit_map(h, &mv, sv, oz::BN));
+    MGW_TRY(oz::digit_map(h, &mvt, svt, oz::BN));
+    MGW_TRY(oz::digit_map(h, &mt, stt, oz::BM));
+    MGW_TRY(oz::digit_map(h, &mw, sww, oz::BM));
+    MGW_CUDA(h, cudaMemcpyAsync(T0, Lov, sizeof(double) * tsz, cudaMemcpyDeviceToDevice, h->stream));
+    for (int n = 0; n < nmom; ++n) {
+      double* Wn = Wmom + (long)n * na2;
+      MGW_TRY(oz::slice_rows(h, naux, ov, T0, ov, stt));
+      MGW_TRY((oz::ozaki_launch(h, mt, mv, stt.exps, sv.exps, naux, naux, (int)ov, oz::ARowsPlain{},
+                                oz::EpiElem<oz::FStore>{oz::FStore{Wn, naux, 1.0, 0.0}}, dstatus, "w_gemm_tc")));
+      if (n + 1 < nmom) {
+        MGW_TRY(oz::slice_rows(h, naux, naux, Wn, naux, sww));
+        MGW_TRY((oz::ozaki_launch(h, mw, mvt, sww.exps, svt.exps, naux, (int)ov, naux, oz::ARowsPlain{},
+                                  oz::EpiElem<oz::FDiagUpdate>{oz::FDiagUpdate{T0, ov, D, 2.0}}, dstatus,
+                                  "t_update_tc")));
+      }
+    }
+    return tc::check_tc_status(h, dstatus, "mgw_response_moments");
+  }
 
   if (o->screening == MGW_TDA) {
     MGW_CUDA(h, cudaMemcpyAsync(T0, Lov, sizeof(double) * tsz, cudaMemcpyDeviceToDevice, h->stream));

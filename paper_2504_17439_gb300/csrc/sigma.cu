@@ -41,17 +41,17 @@ struct EpiBinomialTC {
   int nmom, PB, naux, nmo;
   long ncol;
   BinomCoef bc;
-  __device__ void operator()(int row_local, int col_base, int m0, int n0, int, int N, const long long (&v)[64],
-                             double* smem) const {
-    constexpr int LD = 129;
+  __device__ void operator()(int row_local, int col_base, int m0, int n0, int, int N,
+                             const long long (&v)[oz::kCols], double* smem) const {
+    constexpr int LD = oz::BN + 1;
 #pragma unroll
-    for (int j = 0; j < 64; ++j) smem[row_local * LD + col_base + j] = __longlong_as_double(v[j]);
+    for (int j = 0; j < oz::kCols; ++j) smem[row_local * LD + col_base + j] = __longlong_as_double(v[j]);
     tc::named_bar(1, 256);
     const long g = m0 / 128;
     const int tid = threadIdx.x - 64;
-    const int pairs = PB * 128;
+    const int pairs = PB * oz::BN;
     for (int pi = tid; pi < pairs; pi += 256) {
-      const int pl = pi / 128, col = pi % 128;
+      const int pl = pi / oz::BN, col = pi % oz::BN;
       const long P = g * PB + pl;
       const long n = n0 + col;
       if (P >= naux || n >= N) continue;
@@ -175,11 +175,14 @@ extern "C" mgw_status mgw_sigma_moments(mgw_handle* h, const mgw_options* o, int
   const long ngroups_t = (naux + PBt - 1) / PBt;
   Arena ar;
   double *Z = nullptr, *part = nullptr, *wdig = nullptr, *ldig = nullptr, *st = nullptr;
+  double *adig = nullptr, *zdig = nullptr;
   ar.add(&Z, (size_t)nmom * naux * xc * nmo);
   ar.add(&part, (size_t)nsplit * nmom * n2);
   if (tc) {
     ar.add(&wdig, oz::sliced_doubles(ngroups_t * 128, naux));
     ar.add(&ldig, oz::sliced_doubles((long)xc * nmo, naux));
+    ar.add(&adig, oz::sliced_doubles(nmo, (long)xc * naux));          // GEMM2 A: rows p, K = (x, P)
+    ar.add(&zdig, oz::sliced_doubles((long)nmom * nmo, (long)xc * naux));  // GEMM2 B: rows (n, q)
     ar.add(&st, 1);
   }
   MGW_TRY(ar.commit(h));
@@ -226,6 +229,25 @@ extern "C" mgw_status mgw_sigma_moments(mgw_handle* h, const mgw_options* o, int
         MGW_TRY((dgemm<BM, BN>(h, ngroups * BM, ncol, naux, 1, A, B, epi, "sigma_y_binomial")));
       }
       // Sigma(n) (+)= sum_{P,x} L[P][x][p] Z(n)[(P,x)][q]
+      if (tc) {
+        // on the tensor cores: A rows p, B rows (n, q), both with K = (x_local, P)
+        const long K2 = (long)nx * naux;
+        oz::Sliced sa2, sz2;
+        oz::place_sliced(adig, nmo, K2, sa2);
+        oz::place_sliced(zdig, (long)nmom * nmo, K2, sz2);
+        MGW_TRY(oz::slice_gather(h, nmo, K2, L + (long)x0 * nmo,
+                                 oz::Gather{nmo + 1L, 0, 1, naux, nmo, (long)nmo * nmo}, sa2));
+        MGW_TRY(oz::slice_gather(h, (long)nmom * nmo, K2, Z, oz::Gather{nmo, (long)naux * ncol, 1, naux, nmo, ncol},
+                                 sz2));
+        CUtensorMap ma2, mz2;
+        MGW_TRY(oz::digit_map(h, &ma2, sa2, oz::BM));
+        MGW_TRY(oz::digit_map(h, &mz2, sz2, oz::BN));
+        MGW_TRY((oz::ozaki_launch(h, ma2, mz2, sa2.exps, sz2.exps, nmo, nmom * nmo, (int)K2, oz::ARowsPlain{},
+                                  oz::EpiElem<oz::FSigmaN>{oz::FSigmaN{sig, nmo, first ? 0.0 : 1.0}}, dstatus,
+                                  "sigma_gemm2_tc")));
+        first = false;
+        continue;
+      }
       AKMajor2 A2{L + (long)x0 * nmo, nx, (long)nmo * nmo, nmo, 0};
       BRowMajor B2{Z, nmo, (long)naux * ncol};
       const long K2 = (long)naux * nx;

@@ -64,9 +64,12 @@ def evgw(h: mgw.Handle, eps: torch.Tensor, L: torch.Tensor, nocc: int, nmom_max:
 
 def fsgw(h: mgw.Handle, hcore: torch.Tensor, L: torch.Tensor, eps: torch.Tensor, nocc: int, nmom_max: int,
          screening: int = mgw.MGW_TDA, opts: mgw.Options | None = None, conv_e: float | None = None,
-         conv_mom: float | None = None, max_outer: int = 30, F0: torch.Tensor | None = None) -> dict:
+         conv_mom: float | None = None, max_outer: int = 30, F0: torch.Tensor | None = None,
+         warm: "WarmStart | None" = None) -> dict:
     """Fock self-consistency (Algorithm 2): mgw_fsgw_step until the
-    reference-basis moments and the QP energies stop changing."""
+    reference-basis moments and the QP energies stop changing.  `warm` (a
+    trained WarmStart) predicts the first zeta of every step; the history
+    records the features and targets every step produced."""
     o = opts if opts is not None else mgw.options()
     o.screening = screening
     ce = o.conv_e if conv_e is None else conv_e
@@ -74,6 +77,11 @@ def fsgw(h: mgw.Handle, hcore: torch.Tensor, L: torch.Tensor, eps: torch.Tensor,
     naux, nmo = L.shape[0], L.shape[1]
     nmom = 2 * nmom_max + 2
     dev = L.device
+    # the step reads raw pointers: dense row-major float64 on the device
+    for name, t in (("hcore", hcore), ("L", L), ("eps", eps)):
+        if not t.is_cuda or t.dtype != torch.float64:
+            raise ValueError(f"{name} must be a float64 CUDA tensor")
+    hcore, L, eps = hcore.contiguous(), L.contiguous(), eps.contiguous()
     # canonical reference: F = diag(eps), C = I; otherwise the first step takes
     # the orbitals of F0 itself (init = 1)
     F = torch.diag(eps).contiguous() if F0 is None else F0.clone().contiguous()
@@ -84,6 +92,10 @@ def fsgw(h: mgw.Handle, hcore: torch.Tensor, L: torch.Tensor, eps: torch.Tensor,
     st = mgw.FsgwState(nocc, nmo - nocc, naux, nmom_max, hcore.data_ptr(), L.data_ptr(), F.data_ptr(),
                        C.data_ptr(), e.data_ptr(), eps_qp.data_ptr(), sig.data_ptr(), 0.0, 0.0, 0.0, 0, 0,
                        0 if F0 is None else 1)
+    if warm is not None:
+        st.ws_params = warm.params.data_ptr()
+        st.ws_wbf16 = warm.wbf16.data_ptr()
+        st.ws_width = warm.width
     prev_sig = prev_qp = None
     hist = []
     for outer in range(max_outer):
@@ -91,8 +103,60 @@ def fsgw(h: mgw.Handle, hcore: torch.Tensor, L: torch.Tensor, eps: torch.Tensor,
         dsig = float((sig - prev_sig).abs().max()) if prev_sig is not None else float("inf")
         dqp = float((eps_qp - prev_qp).abs().max()) if prev_qp is not None else float("inf")
         hist.append(dict(outer=outer, inner=st.inner_iters, zeta=st.zeta, dsig=dsig, dqp=dqp, nelec=st.nelec,
-                         zeta_evals=st.zeta_evals))
+                         zeta_evals=st.zeta_evals, feat=list(st.ws_feat), target=st.ws_target, hit=st.ws_hit))
         prev_sig, prev_qp = sig.clone(), eps_qp.clone()
         if dsig < cm and dqp < ce:
             return dict(eps_qp=eps_qp, F=F, zeta=st.zeta, mu=st.mu, converged=True, history=hist)
     return dict(eps_qp=eps_qp, F=F, zeta=st.zeta, mu=st.mu, converged=False, history=hist)
+
+
+class WarmStart:
+    """The learned warm start of the fsGW zeta search: a 3-layer SiLU network
+    (BF16 weights, FP32 accumulation) trained on (features, zeta - zeta_prev)
+    pairs that plain fsGW runs record, with the library's own kernels."""
+
+    def __init__(self, h: mgw.Handle, width: int = 256, seed: int = 0, device="cuda"):
+        self.h = h
+        self.width = width
+        self.dims = (mgw.WS_FEATURES, width, 1)
+        n = h.mgw_mlp_nparams(*self.dims)
+        g = torch.Generator(device="cpu").manual_seed(seed)
+        parts = []
+        for rows, cols in ((width, mgw.WS_FEATURES), (width, 0), (width, width), (width, 0), (1, width), (1, 0)):
+            if cols:
+                parts.append(torch.randn(rows * cols, generator=g) * (1.0 / cols) ** 0.5)
+            else:
+                parts.append(torch.zeros(rows))
+        self.params = torch.cat(parts).float().to(device).contiguous()
+        assert self.params.numel() == n
+        self.wbf16 = torch.empty(n, dtype=torch.bfloat16, device=device)
+        h.mgw_mlp_round(self.params, self.wbf16)
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.step = 0
+        self.scale = 1.0
+
+    def train(self, feats, targets, epochs: int = 400, lr: float = 1e-3, scale: float = 100.0) -> list:
+        """Full-batch Adam on mean-squared error of scale * (zeta - zeta_prev)."""
+        h = self.h
+        self.scale = scale
+        X = torch.as_tensor(feats, dtype=torch.float32, device=self.params.device).contiguous()
+        T = (torch.as_tensor(targets, dtype=torch.float32, device=self.params.device) * scale).reshape(-1, 1)
+        B = X.shape[0]
+        acts = torch.empty((4, B, self.width), dtype=torch.float32, device=X.device)
+        dY = torch.empty((B, 1), dtype=torch.float32, device=X.device)
+        grad = torch.empty_like(self.params)
+        loss = torch.zeros(1, dtype=torch.float32, device=X.device)
+        hist = []
+        for _ in range(epochs):
+            Y = h.mgw_mlp_forward(self.dims, self.params, self.wbf16, X, acts=acts)
+            h.mgw_mlp_mse(Y, T, dY, loss)
+            h.mgw_mlp_backward(self.dims, self.wbf16, X, acts, dY, grad)
+            self.step += 1
+            h.mgw_mlp_adam(self.params, self.wbf16, grad, self.m, self.v, self.step, lr)
+            hist.append(float(loss.item()))
+        # the step reads y in zeta units: fold 1/scale into the last layer
+        n3 = self.width + 1
+        self.params[-n3:] /= scale
+        h.mgw_mlp_round(self.params, self.wbf16)
+        return hist

@@ -50,7 +50,17 @@ class FsgwState(ctypes.Structure):
         ("eps", ctypes.c_void_p), ("eps_qp", ctypes.c_void_p), ("sigma_ref", ctypes.c_void_p),
         ("zeta", ctypes.c_double), ("mu", ctypes.c_double), ("nelec", ctypes.c_double),
         ("inner_iters", ctypes.c_int), ("zeta_evals", ctypes.c_int), ("init", ctypes.c_int),
+        ("ws_params", ctypes.c_void_p), ("ws_wbf16", ctypes.c_void_p), ("ws_width", ctypes.c_int),
+        ("ws_feat", ctypes.c_float * 8), ("ws_target", ctypes.c_double), ("ws_hit", ctypes.c_int),
     ]
+
+WS_FEATURES = 8
+
+
+class System(ctypes.Structure):
+    _fields_ = [("nocc", ctypes.c_int), ("nvir", ctypes.c_int), ("naux", ctypes.c_int),
+                ("eps", ctypes.c_void_p), ("L", ctypes.c_void_p), ("sig_hole", ctypes.c_void_p),
+                ("sig_part", ctypes.c_void_p)]
 
 
 _lib = None
@@ -102,6 +112,17 @@ def load(path: str | None = None):
     lib.mgw_profile_query.restype = _I
     lib.mgw_launch_count.argtypes = [_P]
     lib.mgw_launch_count.restype = ctypes.c_long
+    lib.mgw_mlp_nparams.argtypes = [_I, _I, _I]
+    lib.mgw_mlp_nparams.restype = ctypes.c_long
+    for nm, args in (("mgw_mlp_round", [_P, ctypes.c_long, _P, _P]),
+                     ("mgw_mlp_forward", [_P, _I, _I, _I, _P, _P, _I, _P, _P, _P]),
+                     ("mgw_mlp_backward", [_P, _I, _I, _I, _P, _I, _P, _P, _P, _P]),
+                     ("mgw_mlp_mse", [_P, _I, _I, _P, _P, _P, _P]),
+                     ("mgw_mlp_adam", [_P, ctypes.c_long, _P, _P, _P, _P, _P, _I, ctypes.c_float])):
+        getattr(lib, nm).argtypes = args
+        getattr(lib, nm).restype = _I
+    lib.mgw_sigma_moments_batched.argtypes = [_P, _P, _I, _I, ctypes.POINTER(System)]
+    lib.mgw_sigma_moments_batched.restype = _I
     lib.mgw_fsgw_step.argtypes = [_P, _P, ctypes.POINTER(FsgwState)]
     lib.mgw_fsgw_step.restype = _I
     for name, args in _SIGS.items():
@@ -188,6 +209,63 @@ class Handle:
             raise MgwError(st, (self._lib.mgw_last_error(self._h) or b"").decode())
 
     # -- the ABI entry points, same names ---------------------------------
+    def mgw_sigma_moments_batched(self, opts: Options, nmom, systems):
+        """systems: list of dicts with nocc, nvir, naux, eps, L (device tensors);
+        returns [(sig_hole, sig_part)] per system."""
+        arr = (System * len(systems))()
+        outs = []
+        for i, sy in enumerate(systems):
+            nmo = sy["nocc"] + sy["nvir"]
+            sh = torch.empty((nmom, nmo, nmo), dtype=torch.float64, device=sy["L"].device)
+            sp = torch.empty_like(sh)
+            arr[i] = System(sy["nocc"], sy["nvir"], sy["naux"], _ptr(sy["eps"], (nmo,), "eps"),
+                            _ptr(sy["L"], (sy["naux"], nmo, nmo), "L"), _ptr(sh), _ptr(sp))
+            outs.append((sh, sp))
+        self._check(self._lib.mgw_sigma_moments_batched(self._h, ctypes.byref(opts), len(systems), nmom, arr))
+        return outs
+
+    # -- warm-start network -------------------------------------------------
+    def _fptr(self, t, name):
+        if t is None:
+            return None
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CUDA tensor")
+        if t.dtype not in (torch.float32, torch.bfloat16):
+            raise ValueError(f"{name} must be float32 or bfloat16")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def mgw_mlp_nparams(self, d_in, width, d_out):
+        return int(self._lib.mgw_mlp_nparams(d_in, width, d_out))
+
+    def mgw_mlp_round(self, params, wbf16):
+        self._check(self._lib.mgw_mlp_round(self._h, params.numel(), self._fptr(params, "params"),
+                                            self._fptr(wbf16, "wbf16")))
+
+    def mgw_mlp_forward(self, dims, params, wbf16, X, Y=None, acts=None):
+        d_in, width, d_out = dims
+        B = X.shape[0]
+        Y = Y if Y is not None else torch.empty((B, d_out), dtype=torch.float32, device=X.device)
+        self._check(self._lib.mgw_mlp_forward(self._h, d_in, width, d_out, self._fptr(params, "params"),
+                                              self._fptr(wbf16, "wbf16"), B, self._fptr(X, "X"),
+                                              self._fptr(Y, "Y"), self._fptr(acts, "acts")))
+        return Y
+
+    def mgw_mlp_backward(self, dims, wbf16, X, acts, dY, grad):
+        d_in, width, d_out = dims
+        self._check(self._lib.mgw_mlp_backward(self._h, d_in, width, d_out, self._fptr(wbf16, "wbf16"), X.shape[0],
+                                               self._fptr(X, "X"), self._fptr(acts, "acts"), self._fptr(dY, "dY"),
+                                               self._fptr(grad, "grad")))
+        return grad
+
+    def mgw_mlp_mse(self, Y, T, dY, loss):
+        self._check(self._lib.mgw_mlp_mse(self._h, Y.shape[0], Y.shape[1], self._fptr(Y, "Y"), self._fptr(T, "T"),
+                                          self._fptr(dY, "dY"), self._fptr(loss, "loss")))
+
+    def mgw_mlp_adam(self, params, wbf16, grad, m, v, step, lr):
+        self._check(self._lib.mgw_mlp_adam(self._h, params.numel(), self._fptr(params, "params"),
+                                           self._fptr(wbf16, "wbf16"), self._fptr(grad, "grad"),
+                                           self._fptr(m, "m"), self._fptr(v, "v"), step, float(lr)))
+
     def mgw_fsgw_step(self, opts: Options, st: FsgwState):
         self._check(self._lib.mgw_fsgw_step(self._h, ctypes.byref(opts), ctypes.byref(st)))
         return st
