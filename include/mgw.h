@@ -319,6 +319,33 @@ mgw_status mgw_gemm_fp64_emu(mgw_handle* h, int M, int N, int K,
 mgw_status mgw_gemm_bf16x3(mgw_handle* h, int M, int N, int K,
                            const double* A, const double* B, double* C);
 
+/*
+ * mgw_response_moments_tda_noalloc -- the TDA branch of mgw_response_moments
+ * (same W(n) = eta~(n) V^T, same arguments except the handle) for callers
+ * that cannot allocate device memory: code running where cudaMalloc is
+ * unavailable or forbidden (a host callback, a region that must not
+ * synchronise, a process whose device memory belongs to another allocator,
+ * or embedded callers that size memory up front).  The paper has no
+ * counterpart; this is an interface of this library only.
+ *
+ * It allocates nothing: no cudaMalloc/cudaFree, no library routine that
+ * allocates.  Its scratch (D and the running eta~) is one statically
+ * allocated device array of 4 Mi doubles (32 MiB) that every GPU loading the
+ * library holds until process exit; hence nocc*nvir*(naux + 1) must not
+ * exceed about 4.19e6, else it returns MGW_ERR_UNSUPPORTED without queueing
+ * anything.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress with that device current).  Every call shares the
+ * array and overwrites all of it that it uses; calls whose GPU work overlaps
+ * (other streams, other host threads) race on it and must be serialised by
+ * the caller.
+ *   cuda_stream: cudaStream_t (or NULL) on which the work is queued
+ *   eps_W [nmo], Lov [naux][nocc*nvir] in; Wmom [nmom][naux][naux] out
+ * Returns MGW_ERR_ARG on bad sizes or null pointers, MGW_ERR_CUDA if a launch
+ * or the symbol lookup fails.
+ */
+mgw_status mgw_response_moments_tda_noalloc(void* cuda_stream, int nocc, int nvir, int naux, int nmom,
+                                            const double* eps_W, const double* Lov, double* Wmom);
+
 #ifdef __cplusplus
 }
 #endif
