@@ -405,10 +405,12 @@ extern "C" mgw_status mgw_fsgw_step(mgw_handle* h, const mgw_options* o, mgw_fsg
       const float f[MGW_WS_FEATURES] = {(float)fe[0], (float)fe[1], (float)(fe[1] - fe[0]), (float)g0,
                                         (float)(10.0 * g0), (float)zeta, (float)nocc / (float)nmo, 1.0f};
       for (int i = 0; i < MGW_WS_FEATURES; ++i) st->ws_feat[i] = f[i];
-      bool done = false;
-      if (st->ws_params && st->ws_wbf16 && st->ws_width > 0) {
-        // prediction: zeta_hat = zeta_prev + y; bracket [zeta_prev, zeta_hat] or a
-        // narrow window around zeta_hat, else the plain search below
+      bool done = std::fabs(g0) <= 1e-10;  // the previous zeta still holds
+      if (done) ferr = std::fabs(g0);
+      if (!done && st->ws_params && st->ws_wbf16 && st->ws_width > 0) {
+        // prediction zeta_hat = zeta_prev + y, then the root from the two
+        // points (zeta_prev, g0), (zeta_hat, g_hat); when that fails the
+        // plain search below runs as if there were no prediction
         float* xy = reinterpret_cast<float*>(dots + 96);  // 8 inputs + 1 output
         MGW_CUDA(h, cudaMemcpyAsync(xy, f, sizeof f, cudaMemcpyHostToDevice, h->stream));
         MGW_TRY(mgw_mlp_forward(h, MGW_WS_FEATURES, st->ws_width, 1, st->ws_params, st->ws_wbf16, 1, xy, xy + 8,
@@ -416,20 +418,35 @@ extern "C" mgw_status mgw_fsgw_step(mgw_handle* h, const mgw_options* o, mgw_fsg
         float y = 0.f;
         MGW_CUDA(h, cudaMemcpyAsync(&y, xy + 8, sizeof y, cudaMemcpyDeviceToHost, h->stream));
         MGW_CUDA(h, cudaStreamSynchronize(h->stream));
-        const double zh = std::min(1.0, std::max(-1.0, zeta + (double)y));
+        double zh = std::min(1.0, std::max(-1.0, zeta + (double)y));
+        if (std::fabs(zh - zeta) < 1e-9) zh = zeta + (zeta < 1.0 ? 1e-6 : -1e-6);
         double gh;
         MGW_TRY(cx.gval(st->F, zh, &gh, &evals));
-        double zc = zh, gc = gh;
-        if (std::fabs(gh) > 1e-10) {
-          double a = zeta, ga = g0;
-          if (gh * g0 >= 0) {  // same side: probe a little beyond the prediction
-            const double w = 2e-3 * (zh >= zeta ? 1.0 : -1.0);
-            a = std::min(1.0, std::max(-1.0, zh + w));
-            MGW_TRY(cx.gval(st->F, a, &ga, &evals));
+        // secant steps from the last two points until they bracket the root
+        // (then Illinois, accepted as in the plain search) or hit it
+        double za = zeta, ga = g0, zb = zh, gb = gh, zc = zh, gc = gh;
+        bool bracketed = false;
+        for (int it = 0; it < 4 && std::fabs(gb) > 1e-10; ++it) {
+          if (ga * gb < 0) {
+            MGW_TRY(cx.illinois(st->F, za, ga, zb, gb, &zc, &gc, &evals));
+            bracketed = true;
+            break;
           }
-          if (ga * gh < 0) MGW_TRY(cx.illinois(st->F, a, ga, zh, gh, &zc, &gc, &evals));
+          if (gb == ga) break;
+          const double zs = zb - gb * (zb - za) / (gb - ga);
+          if (!std::isfinite(zs) || zs < -1.0 || zs > 1.0 || std::fabs(zs - zb) > 0.02) break;
+          double gs;
+          MGW_TRY(cx.gval(st->F, zs, &gs, &evals));
+          za = zb;
+          ga = gb;
+          zb = zs;
+          gb = gs;
         }
-        if (std::fabs(gc) <= 1e-6) {
+        if (!bracketed) {
+          zc = zb;
+          gc = gb;
+        }
+        if (std::fabs(gc) <= 1e-10 || (bracketed && std::fabs(gc) <= 1e-6)) {
           zeta = zc;
           ferr = std::fabs(gc);
           done = true;
