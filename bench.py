@@ -267,6 +267,7 @@ def run_gpu(args):
     n2, t2_ms = both("sigma_gemm2")
     nw, tw_ms = both("w_gemm")
     nt, tt_ms = both("t_update")
+    slice_ms = {nm: h.profile_query(nm)[1] for nm in ("slice_rows", "slice_grouped", "slice_cols", "slice_gather")}
     h.profile(False)
     resp_f, y_f, g2_f = work_flops(shape)
     # per launch of the dominant kernel: its share of the Y-stage flops (on the
@@ -329,7 +330,8 @@ def run_gpu(args):
                        "l2": "inputs larger than L2 (L is %.2f GB)" % (L.numel() * 8 / 1e9)},
             "stages_s": {"sigma_build": statistics.mean(build_s), "full_step": statistics.mean(step_s),
                          "w_gemm": tw_ms / 1e3 / args.steps, "t_update": tt_ms / 1e3 / args.steps,
-                         ykern: ty_ms / 1e3 / args.steps, "sigma_gemm2": t2_ms / 1e3 / args.steps},
+                         ykern: ty_ms / 1e3 / args.steps, "sigma_gemm2": t2_ms / 1e3 / args.steps,
+                         **{k: v / 1e3 / args.steps for k, v in slice_ms.items() if v}},
             "gflops_sigma_build": (resp_f + y_f + g2_f) / statistics.mean(build_s) / 1e9,
             "roofline": roofline,
             "e2e": {"value": total_e2e / builds, "unit": "s",

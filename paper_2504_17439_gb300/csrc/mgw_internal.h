@@ -91,6 +91,29 @@ inline mgw_status check_launch(mgw_handle* h, const char* what) {
   return MGW_OK;
 }
 
+// CUDA-event span around the launches queued during its lifetime, recorded
+// under `what` when profiling is on (mgw_profile)
+struct ProfSpan {
+  mgw_handle* h;
+  const char* what;
+  cudaEvent_t ea = nullptr;
+  ProfSpan(mgw_handle* h_, const char* w) : h(h_), what(w) {
+    if (h->prof) {
+      cudaEventCreate(&ea);
+      cudaEventRecord(ea, h->stream);
+    }
+  }
+  ~ProfSpan() {
+    if (!ea) return;
+    cudaEvent_t eb = nullptr;
+    cudaEventCreate(&eb);
+    cudaEventRecord(eb, h->stream);
+    h->spans.push_back({what, ea, eb});
+  }
+  ProfSpan(const ProfSpan&) = delete;
+  ProfSpan& operator=(const ProfSpan&) = delete;
+};
+
 // ---------------------------------------------------------------------------
 // FP64 GEMM  C(m, n) (op)= sum_k A(m, k) B(k, n)
 // 256 threads as a 16 x 16 grid, each owning a (BM/16) x (BN/16) block of

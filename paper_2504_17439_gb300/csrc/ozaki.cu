@@ -5,6 +5,8 @@
 
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 namespace mgw {
 namespace oz {
 
@@ -13,15 +15,40 @@ __device__ __forceinline__ int row_exponent(double mx) {
   return mx > 0.0 ? ilogb(mx) + 2 : 0;
 }
 
-// digits of x 2^-e: balanced base-256, d_s stored as bf16(d_s 2^-8(s-1))
+// digits of x 2^-e: balanced base-256, d_s stored as bf16(d_s 2^-8(s-1)).
+// Integer arithmetic only: X = round(x 2^(56-e)) from the IEEE fields
+// (|X| < 2^55), then d_7, ..., d_2 in [-128, 127] from the low end and
+// d_1 = what is left (|d_1| <= 128), so x 2^-e = sum_s d_s 2^-8s to within
+// half a unit of 2^-56.
 __device__ __forceinline__ void digits_of(double x, int e, __nv_bfloat16 (&d)[kSlices]) {
-  double y = ldexp(x, 8 - e);
-#pragma unroll
-  for (int s = 0; s < kSlices; ++s) {
-    const double q = rint(y);
-    d[s] = __double2bfloat16(ldexp(q, -8 * s));
-    y = (y - q) * 256.0;
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int bexp = (int)((b >> 52) & 0x7FF);
+  unsigned long long m = b & ((1ull << 52) - 1);
+  int ex;  // |x| = m 2^ex
+  if (bexp == 0) {
+    ex = -1074;
+  } else {
+    m |= 1ull << 52;
+    ex = bexp - 1075;
   }
+  const int sh = ex + 56 - e;
+  long long X;
+  if (sh >= 0) {
+    X = (long long)(m << sh);  // sh <= 2 because |x| < 2^(e-1)
+  } else if (sh > -60) {
+    const int r = -sh;
+    X = (long long)((m >> r) + ((m >> (r - 1)) & 1ull));  // nearest, ties away from zero
+  } else {
+    X = 0;
+  }
+  if (b >> 63) X = -X;
+#pragma unroll
+  for (int s = kSlices - 1; s >= 1; --s) {
+    const int dv = (int)((X + 128) & 255) - 128;
+    X = (X - dv) >> 8;
+    d[s] = __float2bfloat16_rn(__int2float_rn(dv) * __int_as_float((127 - 8 * s) << 23));
+  }
+  d[0] = __float2bfloat16_rn(__int2float_rn((int)X));
 }
 
 // source row of a result row: plain (row r of X) or grouped moments
@@ -61,115 +88,124 @@ __global__ void k_slice_rows(long rows, long K, Rows src, __nv_bfloat16* dig, lo
   }
 }
 
-// 32 result rows per CTA (256 threads); result row r, element k = X[k*ldx + r]
-__global__ void k_slice_cols(long rows, long K, const double* __restrict__ X, long ldx, __nv_bfloat16* dig, long ld,
-                             int* exps) {
-  __shared__ double smax[8][32];
-  __shared__ int sexp[32];
-  __shared__ __nv_bfloat16 sd[kSlices][32][65];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const long r0 = (long)blockIdx.x * 32;
-  const long r = r0 + lane;
-  double mx = 0.0;
-  if (r < rows)
-    for (long k = w; k < K; k += 8) mx = fmax(mx, fabs(X[k * ldx + r]));
-  smax[w][lane] = mx;
-  __syncthreads();
-  if (w == 0) {
-    double m = smax[0][lane];
-    for (int i = 1; i < 8; ++i) m = fmax(m, smax[i][lane]);
-    const int e = row_exponent(m);
-    sexp[lane] = e;
-    if (r < rows) exps[r] = e;
-  }
-  __syncthreads();
-  const int e = sexp[lane];
-  const long plane = rows * ld;
-  for (long k0 = 0; k0 < ld; k0 += 64) {
-    for (int kk = w; kk < 64; kk += 8) {
-      const long k = k0 + kk;
-      const double x = (r < rows && k < K) ? X[k * ldx + r] : 0.0;
-      __nv_bfloat16 d[kSlices];
-      digits_of(x, e, d);
-#pragma unroll
-      for (int s = 0; s < kSlices; ++s) sd[s][lane][kk] = d[s];
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < kSlices * 32 * 64; i += 256) {
-      const int s = i / (32 * 64), rr = (i / 64) % 32, kk = i % 64;
-      const long k = k0 + kk;
-      if (r0 + rr < rows && k < ld) dig[s * plane + (r0 + rr) * ld + k] = sd[s][rr][kk];
-    }
-    __syncthreads();
-  }
-}
-
 mgw_status slice_rows(mgw_handle* h, long rows, long K, const double* X, long lds, Sliced& out) {
+  ProfSpan span(h, "slice_rows");
   k_slice_rows<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, h->stream>>>(
       rows, K, RowsPlain{X, lds}, static_cast<__nv_bfloat16*>(out.digits), out.ld, out.exps);
   return check_launch(h, "slice_rows");
 }
 
 mgw_status slice_grouped(mgw_handle* h, int nmom, int PB, int naux, const double* W, Sliced& out) {
+  ProfSpan span(h, "slice_grouped");
   k_slice_rows<<<(unsigned)((out.rows * 32 + 255) / 256), 256, 0, h->stream>>>(
       out.rows, naux, RowsGrouped{W, nmom, PB, naux}, static_cast<__nv_bfloat16*>(out.digits), out.ld, out.exps);
   return check_launch(h, "slice_grouped");
 }
 
-mgw_status slice_cols(mgw_handle* h, long rows, long K, const double* X, long ldx, Sliced& out) {
-  k_slice_cols<<<(unsigned)((rows + 31) / 32), 256, 0, h->stream>>>(
-      rows, K, X, ldx, static_cast<__nv_bfloat16*>(out.digits), out.ld, out.exps);
-  return check_launch(h, "slice_cols");
+// Gathered sources with rows contiguous in memory: element (r, k) sits at
+// X[ro(r) + ko(k)], ro(r) = (r / rdiv) rhi + (r % rdiv) rlo and ko likewise.
+// A lane owns a row, so each warp load is 32 consecutive doubles.
+struct KWalk {  // k -> (k / kdiv, k % kdiv), stepped without dividing
+  long q, rem;
+  const Gather& g;
+  __device__ KWalk(long k, const Gather& g_) : q(k / g_.kdiv), rem(k % g_.kdiv), g(g_) {}
+  __device__ long off() const { return q * g.khi + rem * g.klo; }
+  __device__ void step(int d) {
+    rem += d;
+    if (rem >= g.kdiv) {
+      q += rem / g.kdiv;
+      rem %= g.kdiv;
+    }
+  }
+};
+
+// pass 1: row maxima over a K range per CTA, merged with atomicMax on the
+// bit patterns (non-negative doubles order like their bits)
+__global__ void k_gather_rowmax(long rows, long K, const double* __restrict__ X, Gather g, long kper,
+                                unsigned long long* rmax) {
+  __shared__ double sm[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long r = blockIdx.x * 32L + lane;
+  const long kbeg = blockIdx.y * kper, kend = min(K, kbeg + kper);
+  double m = 0.0;
+  if (r < rows && kbeg + w < kend) {
+    const double* xr = X + (r / g.rdiv) * g.rhi + (r % g.rdiv) * g.rlo;
+    KWalk kw(kbeg + w, g);
+#pragma unroll 4
+    for (long k = kbeg + w; k < kend; k += 8) {
+      m = fmax(m, fabs(xr[kw.off()]));
+      kw.step(8);
+    }
+  }
+  sm[w][lane] = m;
+  __syncthreads();
+  if (w == 0 && r < rows) {
+    for (int i = 1; i < 8; ++i) m = fmax(m, sm[i][lane]);
+    atomicMax(rmax + r, (unsigned long long)__double_as_longlong(m));
+  }
 }
 
-// 32 result rows per CTA (256 threads); element (r, k) = X[roff(r) + koff(k)]
-__global__ void k_slice_gather(long rows, long K, const double* __restrict__ X, Gather g, __nv_bfloat16* dig,
-                               long ld, int* exps) {
-  __shared__ double smax[8][32];
-  __shared__ int sexp[32];
-  __shared__ __nv_bfloat16 sd[kSlices][32][65];
+// pass 2: one 32-row x 64-k tile per CTA; digits staged in shared memory and
+// written along k (128 B per row and digit plane)
+__global__ void k_gather_digits(long rows, long K, const double* __restrict__ X, Gather g,
+                                const unsigned long long* __restrict__ rmax, __nv_bfloat16* dig, long ld,
+                                int* exps) {
+  __shared__ __align__(4) __nv_bfloat16 sd[kSlices][32][66];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const long r0 = (long)blockIdx.x * 32;
-  const long r = r0 + lane;
-  const long ro = r < rows ? (r / g.rdiv) * g.rhi + (r % g.rdiv) * g.rlo : 0;
-  double mx = 0.0;
-  if (r < rows)
-    for (long k = w; k < K; k += 8) mx = fmax(mx, fabs(X[ro + (k / g.kdiv) * g.khi + (k % g.kdiv) * g.klo]));
-  smax[w][lane] = mx;
-  __syncthreads();
-  if (w == 0) {
-    double m = smax[0][lane];
-    for (int i = 1; i < 8; ++i) m = fmax(m, smax[i][lane]);
-    const int e = row_exponent(m);
-    sexp[lane] = e;
-    if (r < rows) exps[r] = e;
+  const long r0 = blockIdx.x * 32L, r = r0 + lane;
+  const long k0 = blockIdx.y * 64L;
+  int e = 0;
+  if (r < rows) {
+    e = row_exponent(__longlong_as_double((long long)rmax[r]));
+    if (blockIdx.y == 0) exps[r] = e;
+  }
+  const double* xr = r < rows ? X + (r / g.rdiv) * g.rhi + (r % g.rdiv) * g.rlo : X;
+  KWalk kw(k0 + w, g);
+#pragma unroll 2
+  for (int kk = w; kk < 64; kk += 8) {
+    const long k = k0 + kk;
+    const double x = (r < rows && k < K) ? xr[kw.off()] : 0.0;
+    kw.step(8);
+    __nv_bfloat16 d[kSlices];
+    digits_of(x, e, d);
+#pragma unroll
+    for (int s = 0; s < kSlices; ++s) sd[s][lane][kk] = d[s];
   }
   __syncthreads();
-  const int e = sexp[lane];
   const long plane = rows * ld;
-  for (long k0 = 0; k0 < ld; k0 += 64) {
-    for (int kk = w; kk < 64; kk += 8) {
-      const long k = k0 + kk;
-      const double x = (r < rows && k < K) ? X[ro + (k / g.kdiv) * g.khi + (k % g.kdiv) * g.klo] : 0.0;
-      __nv_bfloat16 d[kSlices];
-      digits_of(x, e, d);
-#pragma unroll
-      for (int s = 0; s < kSlices; ++s) sd[s][lane][kk] = d[s];
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < kSlices * 32 * 64; i += 256) {
-      const int s = i / (32 * 64), rr = (i / 64) % 32, kk = i % 64;
-      const long k = k0 + kk;
-      if (r0 + rr < rows && k < ld) dig[s * plane + (r0 + rr) * ld + k] = sd[s][rr][kk];
-    }
-    __syncthreads();
+  for (int i = threadIdx.x; i < kSlices * 32 * 32; i += 256) {  // 32-bit words: two k per word
+    const int s = i / (32 * 32), rr = (i / 32) % 32, kp = (i % 32) * 2;
+    if (r0 + rr < rows && k0 + kp < ld)
+      *reinterpret_cast<uint32_t*>(dig + s * plane + (r0 + rr) * ld + k0 + kp) =
+          *reinterpret_cast<const uint32_t*>(&sd[s][rr][kp]);
   }
 }
 
 mgw_status slice_gather(mgw_handle* h, long rows, long K, const double* X, const Gather& g, Sliced& out) {
-  k_slice_gather<<<(unsigned)((rows + 31) / 32), 256, 0, h->stream>>>(
-      rows, K, X, g, static_cast<__nv_bfloat16*>(out.digits), out.ld, out.exps);
-  return check_launch(h, "slice_gather");
+  ProfSpan span(h, "slice_gather");
+  if (rows <= 0) return MGW_OK;
+  if (out.ld == 0) {  // K = 0: no digits, zero exponents
+    MGW_CUDA(h, cudaMemsetAsync(out.exps, 0, sizeof(int) * rows, h->stream));
+    return MGW_OK;
+  }
+  MGW_CUDA(h, cudaMemsetAsync(out.rmax, 0, sizeof(unsigned long long) * rows, h->stream));
+  const long gx = (rows + 31) / 32;
+  // K split so that about eight CTAs per SM run the max pass
+  const long want = std::max(1L, (152L * 8 + gx - 1) / gx);
+  const long ksplit = std::min(want, std::max(1L, (K + 255) / 256));
+  const long kper = (K + ksplit - 1) / ksplit;
+  if (K > 0) {
+    k_gather_rowmax<<<dim3((unsigned)gx, (unsigned)ksplit), 256, 0, h->stream>>>(rows, K, X, g, kper, out.rmax);
+    MGW_TRY(check_launch(h, "gather_rowmax"));
+  }
+  k_gather_digits<<<dim3((unsigned)gx, (unsigned)(out.ld / 64)), 256, 0, h->stream>>>(
+      rows, K, X, g, out.rmax, static_cast<__nv_bfloat16*>(out.digits), out.ld, out.exps);
+  return check_launch(h, "gather_digits");
+}
+
+mgw_status slice_cols(mgw_handle* h, long rows, long K, const double* X, long ldx, Sliced& out) {
+  // element (r, k) = X[k * ldx + r]: a gather with undivided row and k indices
+  return slice_gather(h, rows, K, X, Gather{rows + 1, 0, 1, K + 1, 0, ldx}, out);
 }
 
 mgw_status digit_map(mgw_handle* h, CUtensorMap* map, const Sliced& s, int box_rows) {
@@ -179,7 +215,7 @@ mgw_status digit_map(mgw_handle* h, CUtensorMap* map, const Sliced& s, int box_r
 // bytes of the digit planes + exponents of `rows` x K (in doubles, rounded)
 size_t sliced_doubles(long rows, long K) {
   const long ld = (K + 63) / 64 * 64;
-  return (size_t)((kSlices * rows * ld * 2 + 7) / 8) + (size_t)((rows * 4 + 7) / 8) + 64;
+  return (size_t)((kSlices * rows * ld * 2 + 7) / 8) + (size_t)((rows * 4 + 7) / 8) + (size_t)rows + 64;
 }
 
 struct EpiStoreRows {
@@ -212,6 +248,7 @@ void place_sliced(double* mem, long rows, long K, Sliced& s) {
   s.ld = ld;
   s.digits = mem;
   s.exps = reinterpret_cast<int*>(mem + (kSlices * rows * ld * 2 + 7) / 8);
+  s.rmax = reinterpret_cast<unsigned long long*>(mem + (kSlices * rows * ld * 2 + 7) / 8 + (rows * 4 + 7) / 8);
 }
 }  // namespace oz
 }  // namespace mgw
@@ -228,9 +265,8 @@ extern "C" mgw_status mgw_gemm_fp64_emu(mgw_handle* h, int M, int N, int K, cons
   ar.add(&st, 1);
   MGW_TRY(ar.commit(h));
   Sliced sa, sb;
-  const long ld = (K + 63) / 64 * 64;
-  sa.rows = M; sa.ld = ld; sa.digits = da; sa.exps = reinterpret_cast<int*>(da + (kSlices * (long)M * ld * 2 + 7) / 8);
-  sb.rows = N; sb.ld = ld; sb.digits = db; sb.exps = reinterpret_cast<int*>(db + (kSlices * (long)N * ld * 2 + 7) / 8);
+  place_sliced(da, M, K, sa);
+  place_sliced(db, N, K, sb);
   int* dstatus = reinterpret_cast<int*>(st);
   MGW_CUDA(h, cudaMemsetAsync(dstatus, 0, sizeof(int), h->stream));
   MGW_TRY(slice_rows(h, M, K, A, K, sa));

@@ -17,18 +17,23 @@
 // only this deepest level can afford that.  With S = 7 (28 products) the
 // result carries about 53 bits.
 //
-// CTA: 128 x 96 output tile, 320 threads:
-//   warp 0     TMA producer (digit tiles of A and B, 3D maps: k, row, digit)
-//   warp 1     TMEM allocation (512 columns) and the MMA issuer
-//   warps 2-9  epilogue: warp w reads TMEM lanes 32 (w % 4).., columns
-//              48 ((w - 2) / 4)..; each thread owns 48 elements of one row
+// CTA: 128 x 96 output tile, 384 threads:
+//   warps 0-1  TMA producers (digit tiles of A and B, 3D maps: k, row, digit);
+//              warp p owns barrier groups p and p + 2 and fills their slots,
+//              taking each group's uses in order (a parity wait is sound only
+//              one phase ahead); warp 2 has no role
+//   warp 3     TMEM allocation (512 columns) and the MMA issuer
+//   warps 4-11 epilogue: warp w reads TMEM lanes 32 (w % 4).., columns
+//              48 ((w - 4) / 4)..; each thread owns 48 elements of one row
 // TMEM (512 columns): two FP32 accumulators [0,96) and [96,192) alternate
 // between phases so the flush of one overlaps the MMAs of the next; columns
 // [192,384) hold the level-6..7 integer accumulator (two words per element).
 // The tile is 96 wide so that the levels-2..5 integers (48 x int64 per
-// thread) fit the register budget of a 320-thread block: ten warps put three
-// on one SM sub-partition, whose 16K registers then allow 168 per thread.
-// All waits are time-bounded.
+// thread) fit the register budget of a 384-thread block: twelve warps put
+// three on each SM sub-partition, whose 16K registers allow 168 per thread.
+// Stage slots (one K block of one digit product: 16 KB of A, 12 KB of B)
+// come in groups of two behind one full and one empty barrier, so the MMA
+// thread waits once per eight MMAs.  All waits are time-bounded.
 #pragma once
 
 #include "tc_common.h"
@@ -42,13 +47,79 @@ constexpr int kCols = BN / 2;          // output columns per epilogue thread
 constexpr int kSlices = 7;
 constexpr int kExactTop = 7;          // levels 2..7 accumulated exactly
 constexpr int kRegTop = 5;            // levels 2..5 in registers, 6..7 in TMEM
-constexpr int kThreads = 320;
-constexpr int kStages = 7;
+constexpr int kThreads = 384;
+constexpr int kProducers = 2;   // warps 0..1; warp p fills barrier groups p, p + 2
+constexpr int kMmaWarp = 3;
+constexpr int kEpiWarp0 = 4;    // warps 4..11 (warp 2 has no role)
+static_assert(kThreads / 32 - kEpiWarp0 == 8, "eight epilogue warps, two per TMEM lane quadrant");
+constexpr int kStages = 8;     // stage slots (one K block of one digit product each)
+constexpr int kGroup = 2;      // slots per full/empty barrier
+constexpr int kGroups = kStages / kGroup;
+static_assert(kGroups % kProducers == 0, "each barrier group has one producer warp");
+constexpr int kBand = 8;       // tile rows per band of the launch order (L2 reuse)
 constexpr int kTileBytes = BM * BK * 2;  // one A digit tile (16 KB)
 constexpr int kTileBytesB = BN * BK * 2; // one B digit tile (12 KB)
 constexpr int kStageBytes = kTileBytes + kTileBytesB;
 constexpr int kSmemBytes = 1024 + kStages * kStageBytes + 256;
 constexpr uint64_t kWaitNs = 2000000000ull;
+
+// W 2^E for a nonzero 64-bit integer W, rounded to the nearest double
+// (ties to even) with integer operations only.
+__device__ __forceinline__ double i64_ldexp(long long W, int E) {
+  const bool neg = W < 0;
+  const unsigned long long M = neg ? 0ull - (unsigned long long)W : (unsigned long long)W;
+  const int p = 63 - __clzll((long long)M);
+  unsigned long long mant;
+  int top = p;
+  if (p > 52) {
+    const int r = p - 52;
+    mant = M >> r;
+    const unsigned long long rem = M & ((1ull << r) - 1), half = 1ull << (r - 1);
+    if (rem > half || (rem == half && (mant & 1ull))) ++mant;
+    if (mant >> 53) {
+      mant >>= 1;
+      ++top;
+    }
+  } else {
+    mant = M << (52 - p);
+  }
+  const int be = top + E + 1023;
+  if (be < 1 || be > 2046) return ldexp(neg ? -(double)M : (double)M, E);  // outside the normal range
+  return __longlong_as_double(
+      (long long)(((unsigned long long)neg << 63) | ((unsigned long long)be << 52) | (mant & ((1ull << 52) - 1))));
+}
+
+// (acc 2^-24 + a67 2^-40 + v) 2^E as a double, FP64 units untouched.
+// hi = acc + floor(a67 / 2^16) carries the value in units of 2^-24
+// (|hi| < K 2^39 < 2^63 for K < 2^24); the rest, lo = (a67 mod 2^16) 2^16 +
+// round(v 2^56) in units of 2^-56 (|v| < 2^-1), is folded in at the finest
+// scale 2^-(24+sh), sh <= 32, that keeps hi 2^sh below 2^62.  When sh < 32
+// the result already holds more than 53 bits of hi, so rounding lo to that
+// scale moves it by under half a unit of its last place.
+// round(v 2^56) for |v| < 2^-1 from the float's fields (ties away from zero)
+__device__ __forceinline__ long long f32_fixed56(float v) {
+  const unsigned b = __float_as_uint(v);
+  const int ex = (int)((b >> 23) & 255);
+  const long long m = (long long)((b & 0x7FFFFFu) | (ex ? 0x800000u : 0u));
+  const int sh = (ex ? ex : 1) - 150 + 56;  // |v| 2^56 = m 2^sh, sh <= 31
+  long long r;
+  if (sh >= 0) r = m << sh;
+  else if (sh > -26) r = (m >> -sh) + ((m >> (-sh - 1)) & 1);
+  else r = 0;
+  return (b >> 31) ? -r : r;
+}
+
+__device__ __forceinline__ double combine_parts(long long acc, long long a67, float v, int E) {
+  const long long hi = acc + (a67 >> 16);
+  const long long lo = ((a67 & 0xFFFF) << 16) + f32_fixed56(v);
+  const unsigned long long ah = hi < 0 ? 0ull - (unsigned long long)hi : (unsigned long long)hi;
+  int sh = ah ? __clzll((long long)ah) - 2 : 32;
+  sh = sh > 32 ? 32 : (sh < 0 ? 0 : sh);
+  const long long W = (long long)((unsigned long long)hi << sh) +
+                      ((lo + (sh < 32 ? (1ll << (31 - sh)) : 0)) >> (32 - sh));
+  if (W == 0) return 0.0;
+  return i64_ldexp(W, E - 24 - sh);
+}
 
 __host__ __device__ inline int chunk_of_level(int l) {  // K chunk (multiple of BK) of an exact level
   int c = 1024 / (l - 1);
@@ -91,6 +162,7 @@ struct Schedule {
         }
     }
   }
+  __device__ int items() const { return kSlices * (kSlices + 1) / 2 * kb_total; }  // all 28 products
   __device__ int phases() const {
     int p = 0;
     for (int l = 2; l <= kExactTop; ++l) {
@@ -117,20 +189,26 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
   using namespace tc;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
-  uint64_t* empty = full + kStages;
-  uint64_t* accf = empty + kStages;  // [2] accumulator b ready for the epilogue
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);  // [kGroups]
+  uint64_t* empty = full + kGroups;
+  uint64_t* accf = empty + kGroups;  // [2] accumulator b ready for the epilogue
   uint64_t* acce = accf + 2;         // [2] accumulator b drained by the epilogue
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  // banded tile order: kBand tile rows sweep the tile columns together, so
+  // the CTAs resident at one time share their A and B digit tiles in L2
+  const int MT = (M + BM - 1) / BM, NT = (N + BN - 1) / BN;
+  const int band = (int)(blockIdx.x / (unsigned)(kBand * NT));
+  const int rem = (int)(blockIdx.x % (unsigned)(kBand * NT));
+  const int bh = min(kBand, MT - band * kBand);
+  const int m0 = (band * kBand + rem % bh) * BM, n0 = (rem / bh) * BN;
   const Schedule sched(K);
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+    for (int g = 0; g < kGroups; ++g) {
+      mbar_init(&full[g], 1);
+      mbar_init(&empty[g], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&accf[b], 1);
@@ -138,7 +216,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
     }
     fence_barrier_init();
   }
-  if (warp == 1) {
+  if (warp == kMmaWarp) {
     tmem_alloc(tmem_slot, 512);
     tmem_relinquish();
   }
@@ -147,62 +225,85 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == 0) {
-    if (lane == 0) {
+  if (warp < kProducers) {
+    // the whole warp walks the schedule; one elected lane issues
+    if (warp == 0 && elect_one()) {
       prefetch_tmap(&mA);
       prefetch_tmap(&mB);
-      int it = 0, issued = 0;
-      sched.run([&](int, bool, int, int s, int u, int kb, bool, bool) {
-        const int st = it % kStages;
-        if (!mbar_wait(&empty[st], ((it / kStages) & 1) ^ 1, kWaitNs)) {
-          atomicCAS(status, kOk, kTimeoutEmpty);
-          return false;
-        }
-        uint8_t* sa = smem + st * kStageBytes;
-        mbar_arrive_expect_tx(&full[st], kStageBytes);
-        al.load(&mA, sa, &full[st], kb * BK, m0, s - 1);
-        tma_load_3d(sa + kTileBytes, &mB, &full[st], kb * BK, n0, u - 1);
-        ++it;
-        ++issued;
-        return true;
-      });
-      for (int i = (issued > kStages ? issued - kStages : 0); i < issued; ++i)
-        mbar_wait(&full[i % kStages], (i / kStages) & 1, kWaitNs);
     }
-  } else if (warp == 1) {
-    if (lane == 0) {
-      const uint32_t idesc = idesc_bf16_f32(BM, BN);
-      int it = 0;
-      sched.run([&](int phase, bool, int, int, int, int, bool first, bool last) {
-        const int b = phase & 1, use = phase >> 1;
-        if (first) {
-          if (!mbar_wait(&acce[b], (use & 1) ^ 1, kWaitNs)) {
-            atomicCAS(status, kOk, kTimeoutEpi);
+    __syncwarp();
+    // stage slots come in groups of kGroup behind one full and one empty
+    // barrier; group g uses barrier pair g % kGroups and is issued by the
+    // producer that owns that pair, which takes its pairs' uses in order
+    // (a parity wait is sound only one phase ahead)
+    const int total = sched.items();
+    int it = 0;
+    sched.run([&](int, bool, int, int s, int u, int kb, bool, bool) {
+      const int g = it / kGroup, gs = g % kGroups;
+      if (gs % kProducers == warp) {
+        if (it % kGroup == 0) {
+          if (!mbar_wait(&empty[gs], ((g / kGroups) & 1) ^ 1, kWaitNs)) {
+            if (lane == 0) atomicCAS(status, kOk, kTimeoutEmpty);
             return false;
           }
-          tc_fence_after();
         }
-        const int st = it % kStages;
-        if (!mbar_wait(&full[st], (it / kStages) & 1, kWaitNs)) {
-          atomicCAS(status, kOk, kTimeoutFull);
+        if (elect_one()) {
+          if (it % kGroup == 0)
+            mbar_arrive_expect_tx(&full[gs], (uint32_t)(min(kGroup, total - g * kGroup) * kStageBytes));
+          uint8_t* sa = smem + (it % kStages) * kStageBytes;
+          al.load(&mA, sa, &full[gs], kb * BK, m0, s - 1);
+          tma_load_3d(sa + kTileBytes, &mB, &full[gs], kb * BK, n0, u - 1);
+        }
+        __syncwarp();
+      }
+      ++it;
+      return true;
+    });
+    // before leaving, this producer's groups among the last kGroups have landed
+    const int ng = (it + kGroup - 1) / kGroup;
+    for (int g = (ng > kGroups ? ng - kGroups : 0); g < ng; ++g)
+      if ((g % kGroups) % kProducers == warp) mbar_wait(&full[g % kGroups], (g / kGroups) & 1, kWaitNs);
+  } else if (warp == kMmaWarp) {
+    // the whole warp walks the schedule and waits; one elected lane issues
+    const uint32_t idesc = idesc_bf16_f32(BM, BN);
+    const int total = sched.items();
+    int it = 0;
+    sched.run([&](int phase, bool, int, int, int, int, bool first, bool last) {
+      const int b = phase & 1, use = phase >> 1;
+      if (first) {
+        if (!mbar_wait(&acce[b], (use & 1) ^ 1, kWaitNs)) {
+          if (lane == 0) atomicCAS(status, kOk, kTimeoutEpi);
           return false;
         }
         tc_fence_after();
-        const uint32_t sa = smem_u32(smem + st * kStageBytes);
-        const uint64_t da = sdesc_k128(sa), db = sdesc_k128(sa + kTileBytes);
-        const uint32_t d = tmem + (uint32_t)(b * BN);
+      }
+      // one wait per group of kGroup slots
+      const int g = it / kGroup, gs = g % kGroups;
+      if (it % kGroup == 0) {
+        if (!mbar_wait(&full[gs], (g / kGroups) & 1, kWaitNs)) {
+          if (lane == 0) atomicCAS(status, kOk, kTimeoutFull);
+          return false;
+        }
+        tc_fence_after();
+      }
+      const int st = it % kStages;
+      const uint32_t sa = smem_u32(smem + st * kStageBytes);
+      const uint64_t da = sdesc_k128(sa), db = sdesc_k128(sa + kTileBytes);
+      const uint32_t d = tmem + (uint32_t)(b * BN);
+      if (elect_one()) {
 #pragma unroll
         for (int kk = 0; kk < BK / 16; ++kk)
           mma_bf16(d, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc, (first && kk == 0) ? 0u : 1u);
-        mma_commit(&empty[st]);
+        if (it % kGroup == kGroup - 1 || it == total - 1) mma_commit(&empty[gs]);
         if (last) mma_commit(&accf[b]);
-        ++it;
-        return true;
-      });
-    }
-  } else {
-    // ---------------- epilogue warps 2..9
-    const int quad = warp & 3, half = (warp - 2) >> 2;
+      }
+      __syncwarp();
+      ++it;
+      return true;
+    });
+  } else if (warp >= kEpiWarp0) {
+    // ---------------- epilogue warps 4..11
+    const int quad = warp & 3, half = (warp - kEpiWarp0) >> 2;
     const int row_local = quad * 32 + lane;
     const int col_base = half * kCols;
     long long acc[kCols];
@@ -251,19 +352,22 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
           const float up = l == 6 ? 0x1p32f : 0x1p40f;
           const int shift = 8 * (kExactTop - l);
 #pragma unroll 1
-          for (int c = 0; c < kCols / 8; ++c) {  // 8 elements (16 words) at a time
+          for (int c = 0; c < kCols / 16; ++c) {  // 16 elements (32 words) at a time
             float v[16];
-            tmem_ld16(ta + (c >> 1) * 16, v);
-            uint32_t w[16];
-            tmem_ld16u(tw + 16 * c, w);
+            tmem_ld16(ta + c * 16, v);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              long long t = (long long)(((unsigned long long)w[2 * j + 1] << 32) | w[2 * j]);
-              t += (long long)__float2int_rn(v[(c & 1) * 8 + j] * up) << shift;
-              w[2 * j] = (uint32_t)(unsigned long long)t;
-              w[2 * j + 1] = (uint32_t)((unsigned long long)t >> 32);
+            for (int hh = 0; hh < 2; ++hh) {
+              uint32_t w[16];
+              tmem_ld16u(tw + 32 * c + 16 * hh, w);
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                long long t = (long long)(((unsigned long long)w[2 * j + 1] << 32) | w[2 * j]);
+                t += (long long)__float2int_rn(v[hh * 8 + j] * up) << shift;
+                w[2 * j] = (uint32_t)(unsigned long long)t;
+                w[2 * j + 1] = (uint32_t)((unsigned long long)t >> 32);
+              }
+              tmem_st16u(tw + 32 * c + 16 * hh, w);
             }
-            tmem_st16u(tw + 16 * c, w);
           }
         }
         const int nchunks = (sched.kb_total + chunk_of_level(l) / BK - 1) / (chunk_of_level(l) / BK);
@@ -282,8 +386,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
             const int col = n0 + col_base + e;
             const int fj = col < N ? eb[col] : 0;
             const long long a67 = (long long)(((unsigned long long)w[2 * j + 1] << 32) | w[2 * j]);
-            acc[e] = __double_as_longlong(
-                ldexp((double)acc[e] * 0x1p-24 + (double)a67 * 0x1p-40 + (double)v[(c & 1) * 8 + j], ei + fj - 16));
+            acc[e] = __double_as_longlong(combine_parts(acc[e], a67, v[(c & 1) * 8 + j], ei + fj - 16));
           }
         }
       }
@@ -299,7 +402,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 1) {
+  if (warp == kMmaWarp) {
     tc_fence_after();
     tmem_dealloc(tmem, 512);
   }
@@ -307,9 +410,10 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
 
 // ---- host side
 
-struct Sliced {  // digits [kSlices][rows][ld] BF16 + exponents [rows]
+struct Sliced {  // digits [kSlices][rows][ld] BF16 + exponents [rows] + row maxima scratch [rows]
   void* digits = nullptr;
   int* exps = nullptr;
+  unsigned long long* rmax = nullptr;
   long rows = 0, ld = 0;
 };
 
@@ -334,13 +438,15 @@ template <class ALoad, class Epi>
 mgw_status ozaki_launch(mgw_handle* h, const CUtensorMap& mA, const CUtensorMap& mB, const int* ea,
                         const int* eb, int M, int N, int K, const ALoad& al, const Epi& epi, int* dstatus,
                         const char* what) {
+  if (K >= (1 << 24))  // the exact 128-bit combine of the epilogue needs K < 2^24
+    return fail(h, MGW_ERR_UNSUPPORTED, "%s: K = %d too large for the digit-sliced GEMM", what, K);
   auto kern = ozaki_gemm_kernel<ALoad, Epi>;
   static bool attr = false;
   if (!attr) {
     MGW_CUDA(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
     attr = true;
   }
-  dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM), 1);
+  dim3 grid((unsigned)(((N + BN - 1) / BN) * ((M + BM - 1) / BM)), 1, 1);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (h->prof) {
     cudaEventCreate(&e0);
@@ -370,7 +476,7 @@ struct EpiElem {
                              const long long (&v)[kCols], double*) const {
     const int row = m0 + row_local;
     if (row >= M) return;
-#pragma unroll 4
+#pragma unroll
     for (int j = 0; j < kCols; ++j) {
       const int col = n0 + col_base + j;
       if (col < N) f(row, col, __longlong_as_double(v[j]));

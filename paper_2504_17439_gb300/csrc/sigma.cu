@@ -33,40 +33,49 @@ struct BinomCoef {
 };
 
 // Binomial epilogue of the tensor-core Y stage.  Each of the 256 epilogue
-// threads holds 64 FP64 results of one tile row (t, pl); they are staged in
+// threads holds 48 FP64 results of one tile row (t, pl); they are staged in
 // shared memory (the freed pipeline buffers) and recombined per (pl, column).
+// Z(n) = 2 sum_t C(n,t) s^t e^(n-t) Y(t) is a Taylor shift: with e' = s e,
+// repeated a_t += e' a_(t-1) (t descending, nmom - 1 sweeps) turns a_t = Y(t)
+// into sum_t C(n,t) e'^(n-t) Y(t), and Z(n) = 2 s^n a_n.  NMAX >= nmom bounds
+// the unrolled sweeps so that a[] stays in registers.
+template <int NMAX>
 struct EpiBinomialTC {
   double* Z;
   const double* eps;
   int nmom, PB, naux, nmo;
   long ncol;
-  BinomCoef bc;
-  __device__ void operator()(int row_local, int col_base, int m0, int n0, int, int N,
-                             const long long (&v)[oz::kCols], double* smem) const {
+  double sgn;
+  __device__ __forceinline__ void operator()(int row_local, int col_base, int m0, int n0, int, int N,
+                                             const long long (&v)[oz::kCols], double* smem) const {
     constexpr int LD = oz::BN + 1;
 #pragma unroll
     for (int j = 0; j < oz::kCols; ++j) smem[row_local * LD + col_base + j] = __longlong_as_double(v[j]);
     tc::named_bar(1, 256);
     const long g = m0 / 128;
-    const int tid = threadIdx.x - 64;
+    const int tid = threadIdx.x - 32 * oz::kEpiWarp0;
     const int pairs = PB * oz::BN;
     for (int pi = tid; pi < pairs; pi += 256) {
       const int pl = pi / oz::BN, col = pi % oz::BN;
       const long P = g * PB + pl;
       const long n = n0 + col;
       if (P >= naux || n >= N) continue;
-      const double e = eps[n / nmo];
-      double y[kMaxMom], pe[kMaxMom];
-      pe[0] = 1.0;
-      for (int t = 0; t < nmom; ++t) {
-        y[t] = smem[(t * PB + pl) * LD + col];
-        if (t + 1 < nmom) pe[t + 1] = pe[t] * e;
+      const double es = sgn * eps[n / nmo];
+      double a[NMAX];
+#pragma unroll
+      for (int t = 0; t < NMAX; ++t) a[t] = t < nmom ? smem[(t * PB + pl) * LD + col] : 0.0;
+#pragma unroll
+      for (int j = 1; j < NMAX; ++j) {
+        if (j < nmom) {
+#pragma unroll
+          for (int t = NMAX - 1; t >= j; --t) a[t] = fma(es, a[t - 1], a[t]);
+        }
       }
-      for (int nn = 0; nn < nmom; ++nn) {
-        const double* cr = bc.c + nn * (nn + 1) / 2;
-        double z = 0.0;
-        for (int t = 0; t <= nn; ++t) z = fma(cr[t] * pe[nn - t], y[t], z);
-        Z[((long)nn * naux + P) * ncol + n] = z;
+      double f = 2.0;
+#pragma unroll
+      for (int t = 0; t < NMAX; ++t) {
+        if (t < nmom) Z[((long)t * naux + P) * ncol + n] = f * a[t];
+        f *= sgn;
       }
     }
   }
@@ -219,9 +228,16 @@ extern "C" mgw_status mgw_sigma_moments(mgw_handle* h, const mgw_options* o, int
         MGW_TRY(oz::slice_cols(h, ncol, naux, L + (long)x0 * nmo, (long)nmo * nmo, sl));
         CUtensorMap ml;
         MGW_TRY(oz::digit_map(h, &ml, sl, oz::BN));
-        EpiBinomialTC epi{Z, eps_G + x0, nmom, PBt, naux, nmo, ncol, bc};
-        MGW_TRY((oz::ozaki_launch(h, mw, ml, sw.exps, sl.exps, (int)(ngroups_t * 128), (int)ncol, naux,
-                                  oz::ARowsPlain{}, epi, dstatus, "sigma_y_binomial_tc")));
+        auto launch_y = [&](auto epi) {
+          return oz::ozaki_launch(h, mw, ml, sw.exps, sl.exps, (int)(ngroups_t * 128), (int)ncol, naux,
+                                  oz::ARowsPlain{}, epi, dstatus, "sigma_y_binomial_tc");
+        };
+        if (nmom <= 12)
+          MGW_TRY(launch_y(EpiBinomialTC<12>{Z, eps_G + x0, nmom, PBt, naux, nmo, ncol, sgn}));
+        else if (nmom <= 16)
+          MGW_TRY(launch_y(EpiBinomialTC<16>{Z, eps_G + x0, nmom, PBt, naux, nmo, ncol, sgn}));
+        else
+          MGW_TRY(launch_y(EpiBinomialTC<kMaxMom>{Z, eps_G + x0, nmom, PBt, naux, nmo, ncol, sgn}));
       } else {
         EpiBinomial epi{Z, eps_G + x0, nmom, PB, naux, nmo, ncol, bc};
         AGroupedMoments A{Wmom, nmom, PB, naux, BM};

@@ -54,13 +54,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Wait for the phase with the given parity to complete; false after `limit_ns`.
+// Wait for the phase with the given parity to complete; false after about
+// `limit_ns`.  The bound is kept in SM cycles (2 per ns, at least limit_ns at
+// any clock up to 2 GHz): clock64 is a register read, whereas %globaltimer is
+// slow enough to read that polling it delays every handoff by hundreds of
+// cycles.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = globaltimer();
+  const long long c0 = clock64();
+  const long long limit = (long long)(2 * limit_ns);
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (globaltimer() - t0 > limit_ns) return false;
+    if (clock64() - c0 > limit) return false;
   }
 }
 
@@ -192,6 +197,16 @@ __device__ __forceinline__ void tmem_st16u(uint32_t taddr, const uint32_t (&r)[1
 }
 
 __device__ __forceinline__ uint32_t elect_one_lane() { return (threadIdx.x & 31) == 0; }
+
+// one lane of a converged warp (elect.sync).  Issuing tcgen05.mma from an
+// elected lane while the whole warp walks the loop keeps the tensor pipe
+// fed; a loop run by a lone lane of a diverged warp loses about a hundred
+// cycles of MMA time at every branch.
+__device__ __forceinline__ bool elect_one() {
+  uint32_t pred = 0;
+  asm volatile("{\n\t.reg .pred P;\n\telect.sync _|P, 0xffffffff;\n\tselp.b32 %0, 1, 0, P;\n\t}" : "=r"(pred));
+  return pred != 0;
+}
 
 // named barrier among a subset of warps (ids 1..15; 0 is __syncthreads)
 __device__ __forceinline__ void named_bar(int id, int nthreads) {
