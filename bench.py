@@ -2,9 +2,14 @@
 """Benchmark of the moment-conserving GW self-energy moment build on GB300.
 
 A step is one pass of the hot path over one synthetic molecule-sized system
-(nocc 60, nvir 340, naux 1600, nmom_max 7, TDA, FP64): particle-hole block,
+(nocc 60, nvir 340, naux 1600, nmom_max 7, TDA): particle-hole block,
 response moments W(t), hole/particle Sigma(n) moments, block Lanczos of both
-sectors, and the upfolded-Hamiltonian QP solve.
+sectors, and the upfolded-Hamiltonian QP solve.  By default the bulk
+contractions run as FP64-accurate digit-sliced products on the BF16 tensor
+cores (--precision fp64_tc); --precision fp64 runs them on the FP64 units.
+With the tensor-core path the same run also times the plain FP64 path once
+and reports its Sigma-build time, the speedup and the largest QP-energy
+difference between the two (fp64_path).
 
 Metric: seconds per Sigma-moment build (response + Sigma moments, inputs
 resident in HBM), lower is better.  The JSON line also carries the full step
@@ -14,6 +19,7 @@ the dominant kernel measured live with CUDA events, the CPU oracle timed on
 a bounded sample of the same workload, and SM clocks sampled during the run.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mgw|reference]
+                  [--precision fp64_tc|fp64] [--batched N]
 
 Multi-GPU (torchrun): every rank runs an independent replica of the whole
 step (the path is not sharded here); value = max-over-ranks timed seconds /
@@ -221,16 +227,16 @@ def run_gpu(args):
     sp = torch.empty_like(sh)
     fock = torch.diag(eps).contiguous()
 
-    def step():
+    def step(opts=o):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         ev[0].record(stream)
         h.mgw_extract_ov(nocc, nvir, L, Lov)
-        h.mgw_response_moments(o, nocc, nvir, naux, nmom, eps, Lov, W)
-        h.mgw_sigma_moments(o, nocc, nvir, naux, nmom, eps, L, W, sh, sp)
+        h.mgw_response_moments(opts, nocc, nvir, naux, nmom, eps, Lov, W)
+        h.mgw_sigma_moments(opts, nocc, nvir, naux, nmom, eps, L, W, sh, sp)
         ev[1].record(stream)
-        ch, ah, bh, rh = h.mgw_block_lanczos(o, nmo, nmom, sh)
-        cp, ap, bp, rp = h.mgw_block_lanczos(o, nmo, nmom, sp)
-        qp = h.mgw_qp_solve(o, nmo, nblk, rh, rp, fock, (ch, ah, bh), (cp, ap, bp), 0.0, 2.0 * nocc)
+        ch, ah, bh, rh = h.mgw_block_lanczos(opts, nmo, nmom, sh)
+        cp, ap, bp, rp = h.mgw_block_lanczos(opts, nmo, nmom, sp)
+        qp = h.mgw_qp_solve(opts, nmo, nblk, rh, rp, fock, (ch, ah, bh), (cp, ap, bp), 0.0, 2.0 * nocc)
         ev[2].record(stream)
         return ev, qp
 
@@ -250,7 +256,9 @@ def run_gpu(args):
     barrier()
     t_wall = time.perf_counter()
     torch.cuda.cudart().cudaProfilerStart()  # a profiler started with capture off records this region only
-    recs = [step()[0] for _ in range(args.steps)]
+    outs = [step() for _ in range(args.steps)]
+    recs = [ev for ev, _ in outs]
+    qp_last = outs[-1][1]
     barrier()
     torch.cuda.cudart().cudaProfilerStop()
     t_wall = time.perf_counter() - t_wall
@@ -314,6 +322,21 @@ def run_gpu(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
+    # the plain FP64 GPU path on the same system, once, outside the timed
+    # region: its Sigma-build time and the largest QP-energy difference
+    fp64_path = None
+    if tc and not args.no_compare:
+        o64 = mgw.options(screening=o.screening, precision=mgw.MGW_FP64)
+        step(o64)
+        torch.cuda.synchronize()
+        ev64, qp64 = step(o64)
+        torch.cuda.synchronize()
+        t64 = ev64[0].elapsed_time(ev64[1]) / 1e3
+        dqp = float((qp_last["eps_qp"] - qp64["eps_qp"]).abs().max())
+        fp64_path = {"sigma_build_s": t64, "full_step_s": ev64[0].elapsed_time(ev64[2]) / 1e3,
+                     "speedup_sigma_build": t64 / statistics.mean(build_s),
+                     "qp_max_abs_diff_meV": dqp * 27211.386245988}
+
     total_build = ranks_max(sum(build_s))
     total_step = ranks_max(sum(step_s))
     total_e2e = ranks_max(sum(e2e))
@@ -324,7 +347,8 @@ def run_gpu(args):
         line = {
             "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_step / builds * 1e3, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 digit products -> f64" if tc else "f64", "data": "synthetic",
             "config": {"workload": args.workload, "nocc": nocc, "nvir": nvir, "naux": naux,
                        "nmom_max": shape.nmom_max, "screening": args.screening, "precision": args.precision,
                        "l2": "inputs larger than L2 (L is %.2f GB)" % (L.numel() * 8 / 1e9)},
@@ -338,6 +362,7 @@ def run_gpu(args):
                     "h2d_bytes_per_step": int(L_h.numel() * 8 + eps_h.numel() * 8),
                     "d2h_bytes_per_step": int(2 * sh.numel() * 8)},
             "gpu_launches": launches,
+            "fp64_path": fp64_path,
             "clocks": clk,
             "wall_s": t_wall,
         }
@@ -372,8 +397,10 @@ def run_batched(args):
     o = mgw.options()
     stream = torch.cuda.current_stream()
 
+    outs = h.mgw_sigma_moments_batched(o, nmom, systems)  # tunes tile shapes, captures the graph
+
     def grouped():
-        return h.mgw_sigma_moments_batched(o, nmom, systems)
+        return h.mgw_sigma_moments_batched(o, nmom, systems, out=outs)
 
     def sequential():
         out = []
@@ -417,11 +444,16 @@ def main():
     ap.add_argument("--impl", default="mgw", choices=["mgw", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(mgw_inputs.WORKLOADS))
     ap.add_argument("--screening", default="tda", choices=["tda", "rpa"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp64_tc"])
+    ap.add_argument("--precision", default="fp64_tc", choices=["fp64", "fp64_tc"],
+                    help="fp64_tc: the FP64-accurate digit-sliced tensor-core path (default); fp64: FP64 units")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the one-off plain FP64 comparison run")
+    ap.add_argument("--batched", type=int, default=0, help="uneven batch of N systems instead of one system")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.batched:
+        return run_batched(args)
     return run_gpu(args)
 
 

@@ -68,6 +68,10 @@ typedef struct {
   double conv_e;     /* energy threshold, Ha; default 5 meV = 1.8375e-4 Ha (Sec. IV B) */
   double conv_mom;   /* max |delta Sigma(n)| threshold; default 1e-4 (Sec. IV B) */
   int diis_space;    /* DIIS vectors kept in the Fock loop; default 12 (Sec. IV B) */
+  int batch_graph;   /* mgw_sigma_moments_batched: capture the whole build in a CUDA graph and
+                        replay it while the problem table is unchanged; default 1 */
+  int batch_autotune;/* mgw_sigma_moments_batched: time the candidate tile shapes of each grouped
+                        stage on the first call for a problem table and keep the fastest; default 1 */
 } mgw_options;
 
 /* Fill *o with the defaults listed above. */
@@ -202,6 +206,13 @@ mgw_status mgw_qp_solve(mgw_handle* h, const mgw_options* o,
  * Green's-function index chunks one launch for every Y stage and one for
  * every GEMM2 (a CTA finds its system and tile from a prefix sum of tile
  * counts).  Not in the paper (which treats one molecule at a time).
+ * With o->batch_autotune, the first call for a problem table times the
+ * candidate tile shapes of each stage kind (response GEMM, update, Y stage,
+ * GEMM2) on that table and keeps the fastest; with o->batch_graph the whole
+ * sequence is captured once into a CUDA graph (on a stream the handle owns)
+ * and later calls with the same table (sizes and pointers) and workspace
+ * replay it on the handle's stream.  The graph reads the inputs' current
+ * contents; it is rebuilt when the table, nmom or the workspace changes.
  *   sys: HOST array of nsys descriptors whose pointers are device pointers
  *   1 <= nmom <= 24; o->screening must be MGW_TDA.
  */

@@ -179,6 +179,8 @@ void mgw_options_default(mgw_options* o) {
   o->conv_e = 5.0e-3 / 27.211386245988;
   o->conv_mom = 1e-4;
   o->diis_space = 12;
+  o->batch_graph = 1;
+  o->batch_autotune = 1;
 }
 
 mgw_status mgw_create(mgw_handle** out, int device, void* stream) {
@@ -239,6 +241,8 @@ mgw_status mgw_destroy(mgw_handle* h) {
   if (!h) return MGW_OK;
   cudaStreamSynchronize(h->stream);
   clear_spans(h);
+  if (h->batched_plan_free) h->batched_plan_free(h->batched_plan);
+  if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
   for (auto& sl : h->slots)
     if (sl.first) cudaFree(sl.first);
   if (h->ws) cudaFree(h->ws);

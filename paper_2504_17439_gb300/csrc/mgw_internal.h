@@ -27,6 +27,11 @@ struct mgw_handle {
   bool prof = false;
   struct Span { const char* name; cudaEvent_t a, b; };
   std::vector<Span> spans;
+  // batched Sigma build: the captured graph and tables of the last problem
+  // table, replayed while it is unchanged; a stream of its own to capture on
+  void* batched_plan = nullptr;
+  void (*batched_plan_free)(void*) = nullptr;
+  cudaStream_t capture_stream = nullptr;
 };
 
 namespace mgw {

@@ -36,3 +36,41 @@ def test_batched_sigma_matches_oracle_per_system():
             assert rel(gh[n], rh[n]) < 1e-9, n
             assert rel(gp[n], rp[n]) < 1e-9, n
     h.close()
+
+
+def test_batched_graph_replay_and_plain_issue_agree():
+    """The captured graph replayed on new input values, and the same build
+    issued launch by launch without tuning, both match the oracle."""
+    from paper_2504_17439_gb300 import build, mgw
+
+    build.build()
+    h = mgw.Handle(0)
+    shapes = mgw_inputs.batch_shapes(5, seed=78, nmo_lo=10, nmo_hi=36, nmom_max=2)
+    nmom = 6
+    systems = []
+    for i, sh in enumerate(shapes):
+        eps = mgw_inputs.orbital_energies(sh.nocc, sh.nvir, 600 + i)
+        L = mgw_inputs.df_tensor(sh.naux, sh.nmo, 600 + i) * 2.0
+        systems.append(dict(nocc=sh.nocc, nvir=sh.nvir, naux=sh.naux, eps=torch.from_numpy(eps).cuda(),
+                            L=torch.from_numpy(L).cuda()))
+    o = mgw.options()
+    outs = h.mgw_sigma_moments_batched(o, nmom, systems)  # tune + capture
+    # new values in the same input tensors: the replay must read them
+    for i, (sy, sh) in enumerate(zip(systems, shapes)):
+        sy["eps"].copy_(torch.from_numpy(mgw_inputs.orbital_energies(sh.nocc, sh.nvir, 700 + i)))
+        sy["L"].copy_(torch.from_numpy(mgw_inputs.df_tensor(sh.naux, sh.nmo, 700 + i) * 2.0))
+    launches0 = h.launches
+    outs = h.mgw_sigma_moments_batched(o, nmom, systems, out=outs)  # replay
+    assert h.launches > launches0
+    plain = h.mgw_sigma_moments_batched(mgw.options(batch_graph=0, batch_autotune=0), nmom, systems)
+    for i, ((gh, gp), (ph, pp), sh) in enumerate(zip(outs, plain, shapes)):
+        eps = mgw_inputs.orbital_energies(sh.nocc, sh.nvir, 700 + i)
+        L = mgw_inputs.df_tensor(sh.naux, sh.nmo, 700 + i) * 2.0
+        W = orc.tda_response_moments(orc.particle_hole_block(L, sh.nocc), orc.energy_differences(eps, sh.nocc), nmom)
+        rh, rp = orc.sigma_moments(eps, sh.nocc, L, W)
+        for n in range(nmom):
+            for got in (gh, ph):
+                assert rel(got[n].cpu().numpy(), rh[n]) < 1e-9, (i, n)
+            for got in (gp, pp):
+                assert rel(got[n].cpu().numpy(), rp[n]) < 1e-9, (i, n)
+    h.close()
