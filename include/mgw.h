@@ -344,11 +344,13 @@ mgw_status mgw_gemm_bf16x3(mgw_handle* h, int M, int N, int K,
  * allocated device array of 4 Mi doubles (32 MiB) that every GPU loading the
  * library holds until process exit; hence nocc*nvir*(naux + 1) must not
  * exceed about 4.19e6, else it returns MGW_ERR_UNSUPPORTED without queueing
- * anything.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress with that device current).  Every call shares the
- * array and overwrites all of it that it uses; calls whose GPU work overlaps
- * (other streams, other host threads) race on it and must be serialised by
- * the caller.
+ * anything.  The first call on a device does the set-up: it looks up the
+ * array's device address (cudaGetSymbolAddress with that device current), so
+ * that first call should come before any stream capture.  Every call shares
+ * the array, which keeps the previous call's contents; nothing in it needs
+ * clearing, since D and eta~ are written in full before they are read.
+ * Calls whose GPU work overlaps (other streams, other host threads) race on
+ * the array and must be serialised by the caller.
  *   cuda_stream: cudaStream_t (or NULL) on which the work is queued
  *   eps_W [nmo], Lov [naux][nocc*nvir] in; Wmom [nmom][naux][naux] out
  * Returns MGW_ERR_ARG on bad sizes or null pointers, MGW_ERR_CUDA if a launch
