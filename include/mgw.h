@@ -213,6 +213,13 @@ mgw_status mgw_qp_solve(mgw_handle* h, const mgw_options* o,
  * and later calls with the same table (sizes and pointers) and workspace
  * replay it on the handle's stream.  The graph reads the inputs' current
  * contents; it is rebuilt when the table, nmom or the workspace changes.
+ * With o->precision == MGW_FP64_TC each system instead runs the
+ * single-system FP64-accurate tensor-core pipeline (mgw_response_moments and
+ * mgw_sigma_moments), the systems spread, largest first, over four internal
+ * sub-handles with streams and workspaces of their own so that small systems
+ * run concurrently; the call forks from and joins back to the handle's
+ * stream, and returns after the work has finished (it reads the pipelines'
+ * wait status once at the end).
  *   sys: HOST array of nsys descriptors whose pointers are device pointers
  *   1 <= nmom <= 24; o->screening must be MGW_TDA.
  */

@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <string>
 #include <vector>
 
 namespace mgw {
@@ -229,7 +230,33 @@ static mgw_status issue_all(mgw_handle* h, const std::vector<Sys>& S, const mgw_
   return MGW_OK;
 }
 
+// Tensor-core batched build: the single-system FP64-accurate pipeline per
+// system, systems spread over kBranches sub-handles (stream, workspace and
+// deferred status word each) so that small systems run concurrently.
+constexpr int kBranches = 4;
+struct TcBranches {
+  mgw_handle* sub[kBranches] = {nullptr, nullptr, nullptr, nullptr};
+  cudaStream_t stream[kBranches] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t fork = nullptr, join[kBranches] = {nullptr, nullptr, nullptr, nullptr};
+  int* dstat = nullptr;  // [kBranches]
+  double* lov[kBranches] = {nullptr, nullptr, nullptr, nullptr};
+  double* w[kBranches] = {nullptr, nullptr, nullptr, nullptr};
+  size_t lov_n[kBranches] = {0, 0, 0, 0}, w_n[kBranches] = {0, 0, 0, 0};
+  ~TcBranches() {
+    for (int b = 0; b < kBranches; ++b) {
+      if (sub[b]) mgw_destroy(sub[b]);
+      if (stream[b]) cudaStreamDestroy(stream[b]);
+      if (join[b]) cudaEventDestroy(join[b]);
+      if (lov[b]) cudaFree(lov[b]);
+      if (w[b]) cudaFree(w[b]);
+    }
+    if (fork) cudaEventDestroy(fork);
+    if (dstat) cudaFree(dstat);
+  }
+};
+
 struct BatchedPlan {
+  TcBranches* tcb = nullptr;
   std::vector<long long> shape_key;  // sizes only: the tuned tile shapes stay valid for it
   std::vector<long long> key;        // sizes, pointers, workspace: the graph and tables stay valid
   int cfg[kStKinds] = {0, 0, 0, 0};
@@ -241,6 +268,7 @@ struct BatchedPlan {
   ~BatchedPlan() {
     if (exec) cudaGraphExecDestroy(exec);
     if (dtables) cudaFree(dtables);
+    delete tcb;
   }
 };
 static void free_plan(void* p) { delete static_cast<BatchedPlan*>(p); }
@@ -254,6 +282,96 @@ static mgw_status upload(mgw_handle* h, const Blob& blob, char** d, size_t* byte
     *bytes = blob.b.size();
   }
   if (!blob.b.empty()) MGW_CUDA(h, cudaMemcpy(*d, blob.b.data(), blob.b.size(), cudaMemcpyHostToDevice));
+  return MGW_OK;
+}
+
+static mgw_status grow(mgw_handle* h, double** p, size_t* have, size_t n) {
+  if (*have >= n) return MGW_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *have = 0;
+  MGW_CUDA(h, cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(double)));
+  *have = n;
+  return MGW_OK;
+}
+
+static mgw_status batched_tc(mgw_handle* h, BatchedPlan* plan, const mgw_options* o, int nsys, int nmom,
+                             const mgw_system* sys) {
+  if (!plan->tcb) plan->tcb = new TcBranches();
+  TcBranches& B = *plan->tcb;
+  for (int b = 0; b < kBranches; ++b) {
+    if (!B.stream[b]) MGW_CUDA(h, cudaStreamCreateWithFlags(&B.stream[b], cudaStreamNonBlocking));
+    if (!B.sub[b]) {
+      const mgw_status st = mgw_create(&B.sub[b], h->device, B.stream[b]);
+      if (st != MGW_OK) return fail(h, st, "batched tensor-core build: sub-handle creation failed");
+    }
+    if (!B.join[b]) MGW_CUDA(h, cudaEventCreateWithFlags(&B.join[b], cudaEventDisableTiming));
+  }
+  if (!B.fork) MGW_CUDA(h, cudaEventCreateWithFlags(&B.fork, cudaEventDisableTiming));
+  if (!B.dstat) MGW_CUDA(h, cudaMalloc(reinterpret_cast<void**>(&B.dstat), sizeof(int) * kBranches));
+
+  // largest systems first, each to the least loaded branch (cost ~ Y stage);
+  // a branch's first system is then its largest, so its workspace grows once
+  std::vector<int> order(nsys);
+  std::vector<double> cost(nsys);
+  for (int s = 0; s < nsys; ++s) {
+    const double nmo = sys[s].nocc + sys[s].nvir;
+    cost[s] = (double)sys[s].naux * sys[s].naux * nmo * nmo;
+    order[s] = s;
+  }
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<int> branch(nsys);
+  double load[kBranches] = {0, 0, 0, 0};
+  for (int s : order) {
+    const int b = (int)(std::min_element(load, load + kBranches) - load);
+    branch[s] = b;
+    load[b] += cost[s];
+  }
+  for (int s = 0; s < nsys; ++s) {
+    const int b = branch[s];
+    const long ov = (long)sys[s].nocc * sys[s].nvir;
+    MGW_TRY(grow(h, &B.lov[b], &B.lov_n[b], (size_t)sys[s].naux * ov));
+    MGW_TRY(grow(h, &B.w[b], &B.w_n[b], (size_t)nmom * sys[s].naux * sys[s].naux));
+  }
+
+  long sub_launches0 = 0;
+  for (int b = 0; b < kBranches; ++b) sub_launches0 += B.sub[b]->launches;
+  MGW_CUDA(h, cudaEventRecord(B.fork, h->stream));
+  for (int b = 0; b < kBranches; ++b) {
+    MGW_CUDA(h, cudaStreamWaitEvent(B.stream[b], B.fork, 0));
+    MGW_CUDA(h, cudaMemsetAsync(B.dstat + b, 0, sizeof(int), B.stream[b]));
+    B.sub[b]->defer_status = B.dstat + b;
+  }
+  mgw_status st = MGW_OK;
+  for (int s : order) {
+    const int b = branch[s];
+    mgw_handle* sub = B.sub[b];
+    st = mgw_extract_ov(sub, sys[s].nocc, sys[s].nvir, sys[s].naux, sys[s].L, B.lov[b]);
+    if (st == MGW_OK)
+      st = mgw_response_moments(sub, o, sys[s].nocc, sys[s].nvir, sys[s].naux, nmom, sys[s].eps, B.lov[b], B.w[b]);
+    if (st == MGW_OK)
+      st = mgw_sigma_moments(sub, o, sys[s].nocc, sys[s].nvir, sys[s].naux, nmom, sys[s].eps, sys[s].L, B.w[b],
+                             sys[s].sig_hole, sys[s].sig_part);
+    if (st != MGW_OK) {
+      h->err = std::string("batched tensor-core build, system ") + std::to_string(s) + ": " + sub->err;
+      break;
+    }
+  }
+  for (int b = 0; b < kBranches; ++b) {
+    B.sub[b]->defer_status = nullptr;
+    h->launches += B.sub[b]->launches;
+    MGW_CUDA(h, cudaEventRecord(B.join[b], B.stream[b]));
+    MGW_CUDA(h, cudaStreamWaitEvent(h->stream, B.join[b], 0));
+  }
+  h->launches -= sub_launches0;
+  if (st != MGW_OK) return st;
+  // wait timeouts of any branch, read once after the join
+  int hst[kBranches];
+  MGW_CUDA(h, cudaMemcpyAsync(hst, B.dstat, sizeof hst, cudaMemcpyDeviceToHost, h->stream));
+  MGW_CUDA(h, cudaStreamSynchronize(h->stream));
+  for (int b = 0; b < kBranches; ++b)
+    if (hst[b] != 0)
+      return fail(h, MGW_ERR_TIMEOUT, "batched tensor-core build: pipeline wait timed out (code %d)", hst[b]);
   return MGW_OK;
 }
 
@@ -275,7 +393,15 @@ extern "C" mgw_status mgw_sigma_moments_batched(mgw_handle* h, const mgw_options
     if (sys[s].nocc < 1 || sys[s].nvir < 1 || sys[s].naux < 1 || !sys[s].eps || !sys[s].L || !sys[s].sig_hole ||
         !sys[s].sig_part)
       return fail(h, MGW_ERR_ARG, "mgw_sigma_moments_batched: bad system %d", s);
+  if (o->precision != MGW_FP64 && o->precision != MGW_FP64_TC)
+    return fail(h, MGW_ERR_UNSUPPORTED, "mgw_sigma_moments_batched: precision %d not built", o->precision);
   MGW_CUDA(h, cudaSetDevice(h->device));
+  if (!h->batched_plan) {
+    h->batched_plan = new BatchedPlan();
+    h->batched_plan_free = free_plan;
+  }
+  if (o->precision == MGW_FP64_TC)
+    return batched_tc(h, static_cast<BatchedPlan*>(h->batched_plan), o, nsys, nmom, sys);
   const int rounds = 4;  // Green's-function chunks per sector and system
 
   // workspace per system: D, Lov, T, W, Z (chunked), all in one arena
@@ -329,10 +455,6 @@ extern "C" mgw_status mgw_sigma_moments_batched(mgw_handle* h, const mgw_options
                           (const void*)sys[s].sig_part})
       key.push_back((long long)(uintptr_t)p);
 
-  if (!h->batched_plan) {
-    h->batched_plan = new BatchedPlan();
-    h->batched_plan_free = free_plan;
-  }
   BatchedPlan* plan = static_cast<BatchedPlan*>(h->batched_plan);
   if (plan->key == key && plan->exec && o->batch_graph) {  // replay
     MGW_CUDA(h, cudaGraphLaunch(plan->exec, h->stream));

@@ -32,6 +32,9 @@ struct mgw_handle {
   void* batched_plan = nullptr;
   void (*batched_plan_free)(void*) = nullptr;
   cudaStream_t capture_stream = nullptr;
+  // when set, tensor-core pipelines record wait timeouts here and return
+  // without synchronising; whoever set it reads the word once at the end
+  int* defer_status = nullptr;
 };
 
 namespace mgw {

@@ -209,8 +209,8 @@ extern "C" mgw_status mgw_response_moments(mgw_handle* h, const mgw_options* o, 
   MGW_TRY(energy_differences(h, nocc, nvir, eps_W, D));
 
   if (use_tc) {
-    int* dstatus = reinterpret_cast<int*>(st);
-    MGW_CUDA(h, cudaMemsetAsync(dstatus, 0, sizeof(int), h->stream));
+    int* dstatus = h->defer_status ? h->defer_status : reinterpret_cast<int*>(st);
+    if (!h->defer_status) MGW_CUDA(h, cudaMemsetAsync(dstatus, 0, sizeof(int), h->stream));
     oz::Sliced sv, svt, stt, sww;
     oz::place_sliced(vd, naux, ov, sv);
     oz::place_sliced(vtd, ov, naux, svt);
@@ -236,7 +236,7 @@ extern "C" mgw_status mgw_response_moments(mgw_handle* h, const mgw_options* o, 
                                   "t_update_tc")));
       }
     }
-    return tc::check_tc_status(h, dstatus, "mgw_response_moments");
+    return h->defer_status ? MGW_OK : tc::check_tc_status(h, dstatus, "mgw_response_moments");
   }
 
   if (o->screening == MGW_TDA) {

@@ -197,10 +197,10 @@ extern "C" mgw_status mgw_sigma_moments(mgw_handle* h, const mgw_options* o, int
   MGW_TRY(ar.commit(h));
   oz::Sliced sw, sl;
   CUtensorMap mw;
-  int* dstatus = reinterpret_cast<int*>(st);
+  int* dstatus = h->defer_status ? h->defer_status : reinterpret_cast<int*>(st);
   if (tc) {
     if (nmom > 128) return fail(h, MGW_ERR_UNSUPPORTED, "mgw_sigma_moments: nmom > 128 on the tensor-core path");
-    MGW_CUDA(h, cudaMemsetAsync(dstatus, 0, sizeof(int), h->stream));
+    if (!h->defer_status) MGW_CUDA(h, cudaMemsetAsync(dstatus, 0, sizeof(int), h->stream));
     oz::place_sliced(wdig, ngroups_t * 128, naux, sw);
     MGW_TRY(oz::slice_grouped(h, nmom, PBt, naux, Wmom, sw));
     MGW_TRY(oz::digit_map(h, &mw, sw, oz::BM));
@@ -286,6 +286,6 @@ extern "C" mgw_status mgw_sigma_moments(mgw_handle* h, const mgw_options* o, int
     }
     if (first) MGW_CUDA(h, cudaMemsetAsync(sig, 0, sizeof(double) * nmom * nmo * nmo, h->stream));
   }
-  if (tc) return tc::check_tc_status(h, dstatus, "mgw_sigma_moments");
+  if (tc && !h->defer_status) return tc::check_tc_status(h, dstatus, "mgw_sigma_moments");
   return MGW_OK;
 }

@@ -74,3 +74,32 @@ def test_batched_graph_replay_and_plain_issue_agree():
             for got in (gp, pp):
                 assert rel(got[n].cpu().numpy(), rp[n]) < 1e-9, (i, n)
     h.close()
+
+
+def test_batched_tensor_core_path_matches_oracle():
+    """The tensor-core batched build (per-system FP64-accurate pipelines over
+    concurrent streams) against the oracle, at the FP64 parity tolerance, on
+    two calls in a row (the second reuses the sub-handles' workspaces)."""
+    from paper_2504_17439_gb300 import build, mgw
+
+    build.build()
+    h = mgw.Handle(0)
+    shapes = mgw_inputs.batch_shapes(6, seed=79, nmo_lo=10, nmo_hi=48, nmom_max=2)
+    nmom = 6
+    systems, refs = [], []
+    for i, sh in enumerate(shapes):
+        eps = mgw_inputs.orbital_energies(sh.nocc, sh.nvir, 800 + i)
+        L = mgw_inputs.df_tensor(sh.naux, sh.nmo, 800 + i) * 2.0
+        W = orc.tda_response_moments(orc.particle_hole_block(L, sh.nocc), orc.energy_differences(eps, sh.nocc), nmom)
+        refs.append(orc.sigma_moments(eps, sh.nocc, L, W))
+        systems.append(dict(nocc=sh.nocc, nvir=sh.nvir, naux=sh.naux, eps=torch.from_numpy(eps).cuda(),
+                            L=torch.from_numpy(L).cuda()))
+    o = mgw.options(precision=mgw.MGW_FP64_TC)
+    for call in range(2):
+        outs = h.mgw_sigma_moments_batched(o, nmom, systems)
+        for (gh, gp), (rh, rp) in zip(outs, refs):
+            gh, gp = gh.cpu().numpy(), gp.cpu().numpy()
+            for n in range(nmom):
+                assert rel(gh[n], rh[n]) < 1e-9, (call, n)
+                assert rel(gp[n], rp[n]) < 1e-9, (call, n)
+    h.close()
