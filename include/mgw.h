@@ -122,6 +122,10 @@ mgw_status mgw_extract_ov(mgw_handle* h, int nocc, int nvir, int naux,
  *   Lov   [naux][nocc*nvir]     in   V
  *   Wmom  [nmom][naux][naux]    out  symmetric
  * Requires nocc, nvir, naux >= 1, 1 <= nmom <= 64, D_ia > 0 for RPA.
+ * o->precision MGW_FP64_TC runs every contraction (the recursion's two
+ * products per order and, for the RPA, the products of each quadrature node)
+ * as FP64-accurate digit-sliced tensor-core GEMMs; the RPA's per-node
+ * Cholesky solves stay on the FP64 units.
  */
 mgw_status mgw_response_moments(mgw_handle* h, const mgw_options* o,
                                 int nocc, int nvir, int naux, int nmom,

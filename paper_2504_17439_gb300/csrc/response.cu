@@ -8,15 +8,18 @@
 // and the update, whose epilogue applies the diagonal term in place, so T
 // is read and written once per order and no intermediate is stored.
 //
-// With precision MGW_FP64_TC (TDA) both GEMMs of an order run as
-// FP64-accurate digit-sliced products on the tensor cores (ozaki.h): V is
-// sliced once as rows (for W = T V^T) and once transposed (for W V), T and
-// W(t) are sliced before each use, and the update's epilogue applies
-// T o D + 2 acc exactly as the FP64 kernel does.
+// With precision MGW_FP64_TC both GEMMs of an order run as FP64-accurate
+// digit-sliced products on the tensor cores (ozaki.h): V is sliced once as
+// rows (for W = T V^T) and, for TDA, once transposed (for W V); T and W(t)
+// are sliced before each use, and the update's epilogue applies the
+// diagonal term exactly as the FP64 kernel does.  For the RPA the
+// contractions of the eta~(0) quadrature run on the tensor cores as well;
+// the Cholesky solves of each node stay FP64 (cuSOLVER).
 #include "mgw_internal.h"
 #include "ozaki.h"
 #include "tc_gemm.h"
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -35,6 +38,62 @@ static mgw_status t_update(mgw_handle* h, int naux, long ov, const double* W, co
   return dgemm<64, 64>(h, naux, ov, naux, 1, ARowMajor{W, naux, 0}, BRowMajor{B, ov, 0},
                        EpiDiagUpdate{T, ov, d, alpha}, "t_update");
 }
+
+// The contractions of the RPA path, on the FP64 units or, with `tc`, as
+// FP64-accurate digit-sliced products on the tensor cores (ozaki.h): V is
+// sliced once as rows (the B of every A V^T); A operands are sliced into
+// `ad` and transposed B operands into `bd` right before each product.
+struct RpaProducts {
+  mgw_handle* h;
+  int naux;
+  long ov;
+  const double* V;
+  bool tc;
+  int* dstatus;
+  double *ad, *bd;
+  oz::Sliced sv;
+  CUtensorMap mv;
+
+  // C [naux][naux] = alpha A V^T + beta C, A [naux][ov]
+  mgw_status nt(double alpha, const double* A, double beta, double* C) const {
+    if (!tc) return gemm_nt(h, naux, naux, ov, alpha, A, ov, V, ov, beta, C, naux);
+    oz::Sliced sa;
+    CUtensorMap ma;
+    oz::place_sliced(ad, naux, ov, sa);
+    MGW_TRY(oz::slice_rows(h, naux, ov, A, ov, sa));
+    MGW_TRY(oz::digit_map(h, &ma, sa, oz::BM));
+    return oz::ozaki_launch(h, ma, mv, sa.exps, sv.exps, naux, naux, (int)ov, oz::ARowsPlain{},
+                            oz::EpiElem<oz::FStore>{oz::FStore{C, naux, alpha, beta}}, dstatus, "rpa_nt_tc");
+  }
+  // slices A [naux][naux] as rows and B [naux][ov] as columns (rows ia, K = Q)
+  mgw_status slice_nn(const double* A, const double* B, oz::Sliced& sa, oz::Sliced& sb, CUtensorMap& ma,
+                      CUtensorMap& mb) const {
+    oz::place_sliced(ad, naux, naux, sa);
+    MGW_TRY(oz::slice_rows(h, naux, naux, A, naux, sa));
+    oz::place_sliced(bd, ov, naux, sb);
+    MGW_TRY(oz::slice_cols(h, ov, naux, B, ov, sb));
+    MGW_TRY(oz::digit_map(h, &ma, sa, oz::BM));
+    return oz::digit_map(h, &mb, sb, oz::BN);
+  }
+  // C [naux][ov] = alpha A B + beta C, A [naux][naux], B [naux][ov]
+  mgw_status nn(double alpha, const double* A, const double* B, double beta, double* C) const {
+    if (!tc) return gemm_nn(h, naux, ov, naux, alpha, A, naux, B, ov, beta, C, ov);
+    oz::Sliced sa, sb;
+    CUtensorMap ma, mb;
+    MGW_TRY(slice_nn(A, B, sa, sb, ma, mb));
+    return oz::ozaki_launch(h, ma, mb, sa.exps, sb.exps, naux, (int)ov, naux, oz::ARowsPlain{},
+                            oz::EpiElem<oz::FStore>{oz::FStore{C, ov, alpha, beta}}, dstatus, "rpa_nn_tc");
+  }
+  // T = T o d + alpha A B, A [naux][naux], B [naux][ov]
+  mgw_status upd(const double* A, const double* B, double* T, const double* d, double alpha) const {
+    if (!tc) return t_update(h, naux, ov, A, B, T, d, alpha);
+    oz::Sliced sa, sb;
+    CUtensorMap ma, mb;
+    MGW_TRY(slice_nn(A, B, sa, sb, ma, mb));
+    return oz::ozaki_launch(h, ma, mb, sa.exps, sb.exps, naux, (int)ov, naux, oz::ARowsPlain{},
+                            oz::EpiElem<oz::FDiagUpdate>{oz::FDiagUpdate{T, ov, d, alpha}}, dstatus, "t_update_tc");
+  }
+};
 
 // ---------------------------------------------------------------------------
 // Quadrature for Eqs. 24-25: Clenshaw-Curtis on x in [-1, 1] with nq + 1
@@ -85,8 +144,8 @@ __global__ void k_recip_sq(long n, const double* D, double* r, double* d2) {
 }
 
 // eta~(0) of the RPA, Eqs. 23-28 (see the quadrature note above).
-static mgw_status rpa_eta0(mgw_handle* h, int naux, long ov, int nq, const double* V, const double* D,
-                           double dmin, double dmax, double* T0, double* work) {
+static mgw_status rpa_eta0(mgw_handle* h, const RpaProducts& P, int naux, long ov, int nq, const double* V,
+                           const double* D, double dmin, double dmax, double* T0, double* work) {
   // work layout: G[naux*ov] B1[naux*ov] Q[naux^2] X[naux^2] IQ[naux^2] fac[4*ov]
   const long na2 = (long)naux * naux;
   double* G = work;
@@ -110,7 +169,7 @@ static mgw_status rpa_eta0(mgw_handle* h, int naux, long ov, int nq, const doubl
     MGW_TRY(check_launch(h, "node_factors"));
     // Q = 4 V F D V^T  (Eq. 26)
     MGW_TRY(scale_columns(h, naux, ov, V, fFD, B1));
-    MGW_TRY(gemm_nt(h, naux, naux, ov, 4.0, B1, ov, V, ov, 0.0, Q, naux));
+    MGW_TRY(P.nt(4.0, B1, 0.0, Q));
     // X = Q (I + Q)^-1 - Q  (= Q((I+Q)^-1 - I), Eq. 24; Q and (I+Q)^-1 commute)
     MGW_CUDA(h, cudaMemcpyAsync(X, Q, sizeof(double) * na2, cudaMemcpyDeviceToDevice, h->stream));
     MGW_CUDA(h, cudaMemcpyAsync(IQ, Q, sizeof(double) * na2, cudaMemcpyDeviceToDevice, h->stream));
@@ -121,12 +180,12 @@ static mgw_status rpa_eta0(mgw_handle* h, int naux, long ov, int nq, const doubl
     MGW_TRY(check_launch(h, "sub"));
     // G += (2/pi) w z^2 X (V F)   (integrand even in z: 1/pi over R = 2/pi over [0, inf))
     MGW_TRY(scale_columns(h, naux, ov, V, fF, B1));
-    MGW_TRY(gemm_nn(h, naux, ov, naux, (2.0 / pi) * w[j] * z[j] * z[j], X, naux, B1, ov, 1.0, G, ov));
+    MGW_TRY(P.nn((2.0 / pi) * w[j] * z[j] * z[j], X, B1, 1.0, G));
     // G += 4 w (V D E V^T)(V E)   (Eq. 25)
     MGW_TRY(scale_columns(h, naux, ov, V, fDE, B1));
-    MGW_TRY(gemm_nt(h, naux, naux, ov, 1.0, B1, ov, V, ov, 0.0, Q, naux));
+    MGW_TRY(P.nt(1.0, B1, 0.0, Q));
     MGW_TRY(scale_columns(h, naux, ov, V, fE, B1));
-    MGW_TRY(gemm_nn(h, naux, ov, naux, 4.0 * w[j], Q, naux, B1, ov, 1.0, G, ov));
+    MGW_TRY(P.nn(4.0 * w[j], Q, B1, 1.0, G));
   }
   // eta~(0) = G D^-1 (I - 4 V^T (I + 4 V D^-1 V^T)^-1 V D^-1)   (Eq. 23)
   double* rD = fFD;
@@ -135,12 +194,12 @@ static mgw_status rpa_eta0(mgw_handle* h, int naux, long ov, int nq, const doubl
   MGW_TRY(check_launch(h, "recip"));
   MGW_TRY(scale_columns(h, naux, ov, G, rD, T0));  // T0 = G D^-1
   MGW_TRY(scale_columns(h, naux, ov, V, rD, B1));  // B1 = V D^-1
-  MGW_TRY(gemm_nt(h, naux, naux, ov, 4.0, B1, ov, V, ov, 0.0, Q, naux));  // S - I
+  MGW_TRY(P.nt(4.0, B1, 0.0, Q));  // S - I
   MGW_TRY(add_identity(h, naux, Q, 1.0));
-  MGW_TRY(gemm_nt(h, naux, naux, ov, 1.0, T0, ov, V, ov, 0.0, X, naux));  // Y = G D^-1 V^T
+  MGW_TRY(P.nt(1.0, T0, 0.0, X));  // Y = G D^-1 V^T
   bool not_pd = false;
   MGW_TRY(potrf_potrs(h, naux, Q, naux, X, &not_pd));                      // X = Y S^-1
-  MGW_TRY(gemm_nn(h, naux, ov, naux, -4.0, X, naux, B1, ov, 1.0, T0, ov));
+  MGW_TRY(P.nn(-4.0, X, B1, 1.0, T0));
   return MGW_OK;
 }
 
@@ -178,7 +237,6 @@ extern "C" mgw_status mgw_response_moments(mgw_handle* h, const mgw_options* o, 
     return fail(h, MGW_ERR_ARG, "mgw_response_moments: unknown screening %d", o->screening);
   if (o->screening == MGW_RPA && (o->nquad < 2 || o->nquad % 2))
     return fail(h, MGW_ERR_ARG, "mgw_response_moments: nquad must be even and >= 2");
-  // the response recursion runs on the FP64 units under both FP64 modes
   if (o->precision != MGW_FP64 && o->precision != MGW_FP64_TC)
     return fail(h, MGW_ERR_UNSUPPORTED, "mgw_response_moments: precision %d not built", o->precision);
   MGW_CUDA(h, cudaSetDevice(h->device));
@@ -187,6 +245,7 @@ extern "C" mgw_status mgw_response_moments(mgw_handle* h, const mgw_options* o, 
   const long tsz = (long)naux * ov;
 
   const bool use_tc = o->screening == MGW_TDA && o->precision == MGW_FP64_TC;
+  const bool rpa_tc = o->screening == MGW_RPA && o->precision == MGW_FP64_TC;
   Arena ar;
   double *D = nullptr, *T0 = nullptr, *T1 = nullptr, *aux = nullptr, *work = nullptr, *mm = nullptr;
   double *vd = nullptr, *vtd = nullptr, *td = nullptr, *wd = nullptr, *st = nullptr;
@@ -198,6 +257,13 @@ extern "C" mgw_status mgw_response_moments(mgw_handle* h, const mgw_options* o, 
     ar.add(&vtd, oz::sliced_doubles(ov, naux));
     ar.add(&td, oz::sliced_doubles(naux, ov));
     ar.add(&wd, oz::sliced_doubles(naux, naux));
+    ar.add(&st, 1);
+  }
+  double *ad = nullptr, *bd = nullptr;
+  if (rpa_tc) {  // digit planes: V (rows Q, K = ov), A operands, transposed B operands
+    ar.add(&vd, oz::sliced_doubles(naux, ov));
+    ar.add(&ad, oz::sliced_doubles(naux, std::max<long>(ov, naux)));
+    ar.add(&bd, oz::sliced_doubles(ov, naux));
     ar.add(&st, 1);
   }
   if (o->screening == MGW_RPA) {
@@ -263,13 +329,23 @@ extern "C" mgw_status mgw_response_moments(mgw_handle* h, const mgw_options* o, 
   k_recip_sq<<<(unsigned)((ov + 255) / 256), 256, 0, h->stream>>>(ov, D, rD, D2);
   MGW_TRY(check_launch(h, "recip"));
   MGW_TRY(scale_columns(h, naux, ov, Lov, D, LD));
-  MGW_TRY(rpa_eta0(h, naux, ov, o->nquad, Lov, D, hmm[0], hmm[1], T0, work));
+  RpaProducts P{h, naux, ov, Lov, rpa_tc, nullptr, ad, bd, {}, {}};
+  if (rpa_tc) {
+    P.dstatus = h->defer_status ? h->defer_status : reinterpret_cast<int*>(st);
+    if (!h->defer_status) MGW_CUDA(h, cudaMemsetAsync(P.dstatus, 0, sizeof(int), h->stream));
+    oz::place_sliced(vd, naux, ov, P.sv);
+    MGW_TRY(oz::slice_rows(h, naux, ov, Lov, ov, P.sv));
+    MGW_TRY(oz::digit_map(h, &P.mv, P.sv, oz::BN));
+  }
+  MGW_TRY(rpa_eta0(h, P, naux, ov, o->nquad, Lov, D, hmm[0], hmm[1], T0, work));
   MGW_CUDA(h, cudaMemcpyAsync(T1, LD, sizeof(double) * tsz, cudaMemcpyDeviceToDevice, h->stream));
   double* T[2] = {T0, T1};
   for (int n = 0; n < nmom; ++n) {
     double* Wn = Wmom + (long)n * na2;
-    if (n >= 2) MGW_TRY(t_update(h, naux, ov, Wmom + (long)(n - 2) * na2, LD, T[n & 1], D2, 4.0));
-    MGW_TRY(w_gemm(h, naux, ov, T[n & 1], Lov, Wn));
+    if (n >= 2) MGW_TRY(P.upd(Wmom + (long)(n - 2) * na2, LD, T[n & 1], D2, 4.0));
+    if (rpa_tc) MGW_TRY(P.nt(1.0, T[n & 1], 0.0, Wn));
+    else MGW_TRY(w_gemm(h, naux, ov, T[n & 1], Lov, Wn));
   }
+  if (rpa_tc && !h->defer_status) return tc::check_tc_status(h, P.dstatus, "mgw_response_moments");
   return MGW_OK;
 }

@@ -55,7 +55,8 @@ def system(nocc, nvir, naux, seed, scale=1.0):
 
 
 @pytest.mark.parametrize("shape", SHAPES)
-@pytest.mark.parametrize("screening,precision", [("tda", "fp64"), ("rpa", "fp64"), ("tda", "fp64_tc")])
+@pytest.mark.parametrize("screening,precision", [("tda", "fp64"), ("rpa", "fp64"), ("tda", "fp64_tc"),
+                                                ("rpa", "fp64_tc")])
 def test_response_moments(h, shape, screening, precision):
     from paper_2504_17439_gb300 import mgw
 
