@@ -288,6 +288,18 @@ typedef struct {
 mgw_status mgw_fsgw_step(mgw_handle* h, const mgw_options* o, mgw_fsgw_state* st);
 
 /*
+ * mgw_hf_core -- the core Hamiltonian h = diag(eps) - J[rho] + K[rho]/2 of a
+ * canonical restricted Hartree-Fock reference (rho = 2 on the first nocc
+ * orbitals), i.e. the h for which the Fock build F[rho] = h + J - K/2 of the
+ * fsGW loop (Algorithm 2, Sec. III F) returns diag(eps) at the reference
+ * density; it prepares the inputs of mgw_fsgw_step for a system given by its
+ * orbital energies and DF tensor.
+ *   eps [nmo], L [naux][nmo][nmo] in; hcore [nmo][nmo] out
+ */
+mgw_status mgw_hf_core(mgw_handle* h, int nocc, int nmo, int naux, const double* eps, const double* L,
+                       double* hcore);
+
+/*
  * Warm-start network (not in the paper): three dense layers with SiLU,
  *   z1 = W1 x + b1, a1 = silu(z1); z2 = W2 a1 + b2, a2 = silu(z2); y = W3 a2 + b3.
  * params: FP32 master vector [W1 | b1 | W2 | b2 | W3 | b3] (W row-major

@@ -309,6 +309,43 @@ struct FsgwCtx {
 
 using namespace mgw;
 
+// the closed-shell Hartree-Fock density 2 on the first nocc diagonal
+// elements, and diag(eps) in `d`
+__global__ void k_hf_density(int nmo, int nocc, const double* eps, double* rho, double* d) {
+  const long n2 = (long)nmo * nmo;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n2; i += (long)gridDim.x * blockDim.x) {
+    const int r = (int)(i / nmo), c = (int)(i % nmo);
+    rho[i] = (r == c && r < nocc) ? 2.0 : 0.0;
+    d[i] = r == c ? eps[r] : 0.0;
+  }
+}
+
+extern "C" mgw_status mgw_hf_core(mgw_handle* h, int nocc, int nmo, int naux, const double* eps, const double* L,
+                                  double* hcore) {
+  if (!h) return MGW_ERR_ARG;
+  if (nocc < 1 || nmo <= nocc || naux < 1 || !eps || !L || !hcore)
+    return fail(h, MGW_ERR_ARG, "mgw_hf_core: bad sizes or null pointer");
+  MGW_CUDA(h, cudaSetDevice(h->device));
+  const long n2 = (long)nmo * nmo;
+  Arena ar;
+  double *rho = nullptr, *v = nullptr, *tmp = nullptr;
+  ar.add(&rho, n2);
+  ar.add(&v, naux);
+  ar.add(&tmp, (long)naux * n2);
+  MGW_TRY(ar.commit(h));
+  k_hf_density<<<(unsigned)std::min<long>((n2 + 255) / 256, 152L * 8), 256, 0, h->stream>>>(nmo, nocc, eps, rho,
+                                                                                            hcore);
+  MGW_TRY(check_launch(h, "hf_density"));
+  // hcore = diag(eps) - J[rho] + K[rho]/2: v_P = sum_rs L_Prs rho_rs, J = sum_P v_P L_P
+  MGW_TRY(gemm_nn(h, naux, 1, n2, 1.0, L, n2, rho, 1, 0.0, v, 1));
+  MGW_TRY(gemm_nn(h, 1, n2, naux, -1.0, v, naux, L, n2, 1.0, hcore, n2));
+  // tmp_P = rho L_P; K_pq = sum_{P,r} tmp[P][r][p] L[P][r][q]
+  MGW_TRY((dgemm<64, 64>(h, nmo, nmo, nmo, naux, ARowMajor{rho, nmo, 0}, BRowMajor{L, nmo, n2},
+                         EpiStore{tmp, nmo, n2, 1.0, 0.0}, "gemm_nn")));
+  return dgemm<64, 64>(h, nmo, nmo, (long)naux * nmo, 1, AKMajor2{tmp, nmo, n2, nmo, 0}, BRowMajor{L, nmo, 0},
+                       EpiStore{hcore, nmo, 0, 0.5, 1.0}, "gemm_tn");
+}
+
 extern "C" mgw_status mgw_fsgw_step(mgw_handle* h, const mgw_options* o, mgw_fsgw_state* st) {
   if (!h) return MGW_ERR_ARG;
   mgw_options def;

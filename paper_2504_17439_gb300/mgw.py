@@ -127,6 +127,8 @@ def load(path: str | None = None):
     lib.mgw_sigma_moments_batched.restype = _I
     lib.mgw_fsgw_step.argtypes = [_P, _P, ctypes.POINTER(FsgwState)]
     lib.mgw_fsgw_step.restype = _I
+    lib.mgw_hf_core.argtypes = [_P, _I, _I, _I, _P, _P, _P]
+    lib.mgw_hf_core.restype = _I
     for name, args in _SIGS.items():
         fn = getattr(lib, name)
         fn.argtypes = [_P] + args
@@ -230,6 +232,14 @@ class Handle:
             outs.append((sh, sp))
         self._check(self._lib.mgw_sigma_moments_batched(self._h, ctypes.byref(opts), len(systems), nmom, arr))
         return outs
+
+    def mgw_hf_core(self, nocc, eps, L):
+        """h = diag(eps) - J[rho_HF] + K[rho_HF]/2 (F[rho_HF] = diag(eps))."""
+        naux, nmo = L.shape[0], L.shape[1]
+        hc = torch.empty((nmo, nmo), dtype=torch.float64, device=L.device)
+        self._check(self._lib.mgw_hf_core(self._h, nocc, nmo, naux, _ptr(eps, (nmo,), "eps"),
+                                          _ptr(L, (naux, nmo, nmo), "L"), _ptr(hc)))
+        return hc
 
     # -- warm-start network -------------------------------------------------
     def _fptr(self, t, name):

@@ -54,3 +54,18 @@ def test_fsgw_from_a_rotated_start_matches(h):
                      F0=torch.from_numpy(U.T @ np.diag(eps) @ U).cuda())
     assert r0["converged"] and r1["converged"]
     assert np.abs(r1["eps_qp"].cpu().numpy() - r0["eps_qp"].cpu().numpy()).max() < 1e-6
+
+
+@pytest.mark.parametrize("nocc,nvir,naux,seed", [(3, 9, 30, 41), (7, 30, 130, 42), (1, 1, 1, 43)])
+def test_hf_core_matches_oracle(nocc, nvir, naux, seed):
+    """mgw_hf_core against the oracle's h = diag(eps) - J[rho_HF] + K[rho_HF]/2."""
+    from paper_2504_17439_gb300 import build, mgw
+
+    build.build()
+    h = mgw.Handle(0)
+    eps = mgw_inputs.orbital_energies(nocc, nvir, seed)
+    L = mgw_inputs.df_tensor(naux, nocc + nvir, seed) * 2.0
+    ref = orc.hf_core_hamiltonian(eps, L, nocc)
+    got = h.mgw_hf_core(nocc, torch.from_numpy(eps).cuda(), torch.from_numpy(L).cuda()).cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
+    h.close()
