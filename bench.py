@@ -483,29 +483,35 @@ def run_fsgw(args):
             out.append((nocc, eps, L, h.mgw_hf_core(nocc, eps, L)))
         return out
 
-    def run(sy, warm=None):
+    def run(sy, warm=None, warm_fock=None):
         nocc, eps, L, hc = sy
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        r = driver.fsgw(h, hc, L, eps, nocc, 5, opts=o, conv_e=1e-6, conv_mom=1e-5, max_outer=40, warm=warm)
+        r = driver.fsgw(h, hc, L, eps, nocc, 5, opts=o, conv_e=1e-6, conv_mom=1e-5, max_outer=40, warm=warm,
+                        warm_fock=warm_fock)
         torch.cuda.synchronize()
         r["seconds"] = time.perf_counter() - t0
         return r
 
-    feats, targets = [], []
+    feats, targets, ffeats, ftargets = [], [], [], []
     for sy in systems(2 * args.fsgw, mgw_inputs.SEED_BASE + 400):
         r = run(sy)
         for st in r["history"]:
             feats.append(st["feat"])
             targets.append(st["target"])
+            if st["fock_valid"]:
+                ffeats.append(st["fock_feat"])
+                ftargets.append(st["fock_target"])
     net = driver.WarmStart(h, width=256, seed=1)
     losses = net.train(np.array(feats), np.array(targets), epochs=600, lr=1e-3)
+    net_f = driver.WarmStart(h, width=256, seed=2)
+    losses_f = net_f.train(np.array(ffeats), np.array(ftargets), epochs=600, lr=1e-3, scale=1.0)
     agg = {k: {"seconds": 0.0, "outer": 0, "inner": 0, "zeta_evals": 0, "converged": 0} for k in ("plain", "warm")}
     dqp = 0.0
     nmos = []
     for sy in systems(args.fsgw, mgw_inputs.SEED_BASE + 500):
         nmos.append(sy[2].shape[1])
-        rp, rw = run(sy), run(sy, warm=net)
+        rp, rw = run(sy), run(sy, warm=net, warm_fock=net_f)
         for k, r in (("plain", rp), ("warm", rw)):
             agg[k]["seconds"] += r["seconds"]
             agg[k]["outer"] += len(r["history"])
@@ -519,10 +525,13 @@ def run_fsgw(args):
             "data": "synthetic",
             "config": {"workload": "fsgw held-out systems", "systems": n, "nmo": nmos, "naux": "4 nmo",
                        "nmom_max": 5, "train_systems": 2 * n, "train_pairs": len(targets),
-                       "conv_qp_ha": 1e-6},
+                       "fock_train_pairs": len(ftargets), "conv_qp_ha": 1e-6,
+                       "warm": "zeta warm start and Fock-matrix proposal"},
             "plain": agg["plain"], "warm": agg["warm"],
             "speedup_vs_plain": agg["plain"]["seconds"] / max(agg["warm"]["seconds"], 1e-12),
             "train_loss_first_last": [losses[0], losses[-1]],
+            "fock_train_loss_first_last": [losses_f[0], losses_f[-1]],
+            "fock_targets_mean_std": [float(np.mean(ftargets)), float(np.std(ftargets))],
             "max_qp_diff_warm_vs_plain_meV": dqp * 27211.386245988}
     print(json.dumps(line), flush=True)
     h.close()

@@ -281,6 +281,21 @@ typedef struct {
   float ws_feat[8];       /* host out: the features of the first search */
   double ws_target;       /* host out: zeta found by it minus zeta_prev (a training target) */
   int ws_hit;             /* host out: 1 if the predicted bracket held the root */
+  /* learned Fock-matrix proposal (not in the paper): with F_prev != NULL and
+   * fock_hist = 1, the step first moves F to F + beta (F - F_prev), beta from
+   * a network of the same family (d_in = MGW_WS_FEATURES, d_out = 1, input
+   * wf_feat, clamped to [-0.5, 2]); the plain DIIS Fock loop then starts from
+   * it (NULL wf_params: beta = 0).  At the end the step sets F_prev to its
+   * own starting F and fock_hist = 1. */
+  double* F_prev;         /* [nmo][nmo] in/out, or NULL: no proposal, nothing recorded */
+  int fock_hist;          /* host in/out: 1 when F_prev holds the previous step's start */
+  const float* wf_params;
+  const unsigned short* wf_wbf16;
+  int wf_width;
+  float wf_feat[8];       /* host out: the proposal's features (zero without history) */
+  double wf_target;       /* host in/out: least-squares beta that reaches the step's converged F
+                             along F - F_prev (a training target); read as a feature next step */
+  double wf_beta;         /* host out: the beta applied */
 } mgw_fsgw_state;
 
 #define MGW_WS_FEATURES 8

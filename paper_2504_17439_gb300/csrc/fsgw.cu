@@ -388,6 +388,11 @@ extern "C" mgw_status mgw_fsgw_step(mgw_handle* h, const mgw_options* o, mgw_fsg
   MGW_TRY(slot_buffer(h, 22, 4 * n2, &misc));
   MGW_TRY(slot_buffer(h, 23, 128, &dots));
   MGW_TRY(slot_buffer(h, 24, naux, &v));
+  double *Forig = nullptr, *Fstep = nullptr;  // the step's starting F, and F - F_prev
+  if (st->F_prev) {
+    MGW_TRY(slot_buffer(h, 25, n2, &Forig));
+    MGW_TRY(slot_buffer(h, 26, n2, &Fstep));
+  }
   MGW_CUDA(h, cudaMemsetAsync(dE, 0, sizeof(double) * space * n2, h->stream));
 
   if (st->init) {  // orbitals of the given Fock matrix
@@ -425,6 +430,47 @@ extern "C" mgw_status mgw_fsgw_step(mgw_handle* h, const mgw_options* o, mgw_fsg
 
   FsgwCtx cx{h, o, nmo, naux, nblk, rh, rp, n2, st->h, st->L, crh, ah, bh, crp, ap, bp,
              E, weight, epsqp, rho, rho_old, Fn, tmpL, v, dots, 2.0 * nocc};
+  // Fock-matrix proposal: F <- F + beta (F - F_prev), beta from the network
+  // (none: beta = 0, the plain start); the DIIS loop below starts from it
+  st->wf_beta = 0.0;
+  const double prev_target = st->wf_target;
+  st->wf_target = 0.0;
+  for (int i = 0; i < MGW_WS_FEATURES; ++i) st->wf_feat[i] = 0.f;
+  double dd = 0.0;  // |F - F_prev|^2
+  if (st->F_prev) {
+    MGW_CUDA(h, cudaMemcpyAsync(Forig, st->F, sizeof(double) * n2, cudaMemcpyDeviceToDevice, h->stream));
+    if (st->fock_hist) {
+      k_sub<<<nbk(n2), 256, 0, h->stream>>>(n2, st->F, st->F_prev, Fstep);
+      k_maxabs_diff<<<1, 256, 0, h->stream>>>(n2, st->F, st->F_prev, dots + 104);
+      k_dots<<<1, 256, 0, h->stream>>>(n2, 1, Fstep, Fstep, n2, dots + 105);
+      MGW_TRY(check_launch(h, "fock_step"));
+      double hv[2], fe[2];
+      MGW_CUDA(h, cudaMemcpyAsync(hv, dots + 104, sizeof hv, cudaMemcpyDeviceToHost, h->stream));
+      MGW_CUDA(h, cudaMemcpyAsync(fe, st->eps + nocc - 1, sizeof fe, cudaMemcpyDeviceToHost, h->stream));
+      MGW_CUDA(h, cudaStreamSynchronize(h->stream));
+      dd = hv[1];
+      const float f[MGW_WS_FEATURES] = {(float)(std::log10(hv[0] + 1e-14) / 10.0), (float)(10.0 * hv[0]),
+                                        (float)prev_target, (float)(prev_target != 0.0), (float)st->zeta,
+                                        (float)(fe[1] - fe[0]), (float)nocc / (float)nmo, 1.0f};
+      for (int i = 0; i < MGW_WS_FEATURES; ++i) st->wf_feat[i] = f[i];
+      if (st->wf_params && st->wf_wbf16 && st->wf_width > 0 && dd > 0.0) {
+        float* xy = reinterpret_cast<float*>(dots + 112);  // 8 inputs + 1 output
+        MGW_CUDA(h, cudaMemcpyAsync(xy, f, sizeof f, cudaMemcpyHostToDevice, h->stream));
+        MGW_TRY(mgw_mlp_forward(h, MGW_WS_FEATURES, st->wf_width, 1, st->wf_params, st->wf_wbf16, 1, xy, xy + 8,
+                                nullptr));
+        float y = 0.f;
+        MGW_CUDA(h, cudaMemcpyAsync(&y, xy + 8, sizeof y, cudaMemcpyDeviceToHost, h->stream));
+        MGW_CUDA(h, cudaStreamSynchronize(h->stream));
+        const double beta = std::min(2.0, std::max(-0.5, (double)y));
+        if (std::isfinite(beta) && beta != 0.0) {
+          k_axpby<<<nbk(n2), 256, 0, h->stream>>>(n2, beta, Fstep, 1.0, st->F);
+          MGW_TRY(check_launch(h, "fock_proposal"));
+          st->wf_beta = beta;
+        }
+      }
+    }
+  }
+
   // 3. zeta / Fock rounds
   int inner = 0, evals = 0;
   double zeta = st->zeta;
@@ -501,6 +547,21 @@ extern "C" mgw_status mgw_fsgw_step(mgw_handle* h, const mgw_options* o, mgw_fsg
     double now = 0;
     MGW_TRY(cx.nerr(st->F, zeta, &now));
     if (now <= std::max(ferr, 1e-10) + 1e-12 && k <= 2) break;
+  }
+  // the beta that would have started at the converged F along F - F_prev
+  // (least squares, a training target); F_prev <- this step's starting F
+  if (st->F_prev) {
+    if (st->fock_hist && dd > 0.0) {
+      k_sub<<<nbk(n2), 256, 0, h->stream>>>(n2, st->F, Forig, Fn);
+      k_dots<<<1, 256, 0, h->stream>>>(n2, 1, Fn, Fstep, n2, dots + 106);
+      MGW_TRY(check_launch(h, "fock_target"));
+      double ed = 0.0;
+      MGW_CUDA(h, cudaMemcpyAsync(&ed, dots + 106, sizeof ed, cudaMemcpyDeviceToHost, h->stream));
+      MGW_CUDA(h, cudaStreamSynchronize(h->stream));
+      st->wf_target = ed / dd;
+    }
+    MGW_CUDA(h, cudaMemcpyAsync(st->F_prev, Forig, sizeof(double) * n2, cudaMemcpyDeviceToDevice, h->stream));
+    st->fock_hist = 1;
   }
   // 4. new orbitals and the QP energies in their basis
   MGW_CUDA(h, cudaMemcpyAsync(misc, st->F, sizeof(double) * n2, cudaMemcpyDeviceToDevice, h->stream));

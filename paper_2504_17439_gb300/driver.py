@@ -65,11 +65,13 @@ def evgw(h: mgw.Handle, eps: torch.Tensor, L: torch.Tensor, nocc: int, nmom_max:
 def fsgw(h: mgw.Handle, hcore: torch.Tensor, L: torch.Tensor, eps: torch.Tensor, nocc: int, nmom_max: int,
          screening: int = mgw.MGW_TDA, opts: mgw.Options | None = None, conv_e: float | None = None,
          conv_mom: float | None = None, max_outer: int = 30, F0: torch.Tensor | None = None,
-         warm: "WarmStart | None" = None) -> dict:
+         warm: "WarmStart | None" = None, warm_fock: "WarmStart | None" = None) -> dict:
     """Fock self-consistency (Algorithm 2): mgw_fsgw_step until the
     reference-basis moments and the QP energies stop changing.  `warm` (a
-    trained WarmStart) predicts the first zeta of every step; the history
-    records the features and targets every step produced."""
+    trained WarmStart) predicts the first zeta of every step; `warm_fock`
+    predicts the step beta of the Fock-matrix proposal F + beta (F - F_prev)
+    that the step's DIIS loop starts from.  The history records the features
+    and targets of both that every step produced."""
     o = opts if opts is not None else mgw.options()
     o.screening = screening
     ce = o.conv_e if conv_e is None else conv_e
@@ -96,6 +98,13 @@ def fsgw(h: mgw.Handle, hcore: torch.Tensor, L: torch.Tensor, eps: torch.Tensor,
         st.ws_params = warm.params.data_ptr()
         st.ws_wbf16 = warm.wbf16.data_ptr()
         st.ws_width = warm.width
+    F_prev = torch.empty_like(F)
+    st.F_prev = F_prev.data_ptr()
+    st.fock_hist = 0
+    if warm_fock is not None:
+        st.wf_params = warm_fock.params.data_ptr()
+        st.wf_wbf16 = warm_fock.wbf16.data_ptr()
+        st.wf_width = warm_fock.width
     prev_sig = prev_qp = None
     hist = []
     for outer in range(max_outer):
@@ -103,7 +112,9 @@ def fsgw(h: mgw.Handle, hcore: torch.Tensor, L: torch.Tensor, eps: torch.Tensor,
         dsig = float((sig - prev_sig).abs().max()) if prev_sig is not None else float("inf")
         dqp = float((eps_qp - prev_qp).abs().max()) if prev_qp is not None else float("inf")
         hist.append(dict(outer=outer, inner=st.inner_iters, zeta=st.zeta, dsig=dsig, dqp=dqp, nelec=st.nelec,
-                         zeta_evals=st.zeta_evals, feat=list(st.ws_feat), target=st.ws_target, hit=st.ws_hit))
+                         zeta_evals=st.zeta_evals, feat=list(st.ws_feat), target=st.ws_target, hit=st.ws_hit,
+                         fock_feat=list(st.wf_feat), fock_target=st.wf_target, fock_beta=st.wf_beta,
+                         fock_valid=outer > 0))
         prev_sig, prev_qp = sig.clone(), eps_qp.clone()
         if dsig < cm and dqp < ce:
             return dict(eps_qp=eps_qp, F=F, zeta=st.zeta, mu=st.mu, converged=True, history=hist)

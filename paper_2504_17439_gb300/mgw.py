@@ -54,6 +54,9 @@ class FsgwState(ctypes.Structure):
         ("inner_iters", ctypes.c_int), ("zeta_evals", ctypes.c_int), ("init", ctypes.c_int),
         ("ws_params", ctypes.c_void_p), ("ws_wbf16", ctypes.c_void_p), ("ws_width", ctypes.c_int),
         ("ws_feat", ctypes.c_float * 8), ("ws_target", ctypes.c_double), ("ws_hit", ctypes.c_int),
+        ("F_prev", ctypes.c_void_p), ("fock_hist", ctypes.c_int),
+        ("wf_params", ctypes.c_void_p), ("wf_wbf16", ctypes.c_void_p), ("wf_width", ctypes.c_int),
+        ("wf_feat", ctypes.c_float * 8), ("wf_target", ctypes.c_double), ("wf_beta", ctypes.c_double),
     ]
 
 WS_FEATURES = 8
