@@ -193,6 +193,28 @@ def run_reference(args):
     return 0
 
 
+# ---------------------------------------------------------------------------- ranks
+
+
+def ranks_max(x, world, device):
+    """The largest value of x over the job's ranks (the slowest rank's time)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_seconds_per_build(slowest_rank_seconds, steps, world):
+    """Seconds per Sigma build of the whole job: every rank runs `steps`
+    builds of its own replica (weak scaling), and the job lasts as long as
+    its slowest rank."""
+    return slowest_rank_seconds / (steps * world)
+
+
 # ---------------------------------------------------------------------------- GPU arm
 
 
@@ -315,13 +337,6 @@ def run_gpu(args):
         if i >= args.warmup:
             e2e.append(a.elapsed_time(b) / 1e3)
 
-    def ranks_max(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     # the plain FP64 GPU path on the same system, once, outside the timed
     # region: its Sigma-build time and the largest QP-energy difference
     fp64_path = None
@@ -337,11 +352,11 @@ def run_gpu(args):
                      "speedup_sigma_build": t64 / statistics.mean(build_s),
                      "qp_max_abs_diff_meV": dqp * 27211.386245988}
 
-    total_build = ranks_max(sum(build_s))
-    total_step = ranks_max(sum(step_s))
-    total_e2e = ranks_max(sum(e2e))
+    total_build = ranks_max(sum(build_s), world, "cuda")
+    total_step = ranks_max(sum(step_s), world, "cuda")
+    total_e2e = ranks_max(sum(e2e), world, "cuda")
     builds = args.steps * world
-    value = total_build / builds
+    value = job_seconds_per_build(total_build, args.steps, world)
     line = None
     if rank == 0:
         line = {

@@ -1,0 +1,58 @@
+"""Host logic of the multi-GPU bench on CPU ranks (gloo, world size 2): the
+job's time is its slowest rank's, the value counts every rank's builds, and
+the reference arm prints only on rank 0."""
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    import torch.distributed as dist
+
+    import bench
+
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    local = [3.0, 5.0][rank]  # each rank's summed build seconds
+    slowest = bench.ranks_max(local, world, "cpu")
+    out[rank] = (slowest, bench.job_seconds_per_build(slowest, 4, world))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_ranks_take_the_slowest_rank_and_count_all_builds():
+    world = 2
+    manager = mp.get_context("spawn").Manager()
+    out = manager.dict()
+    mp.start_processes(_worker, args=(world, _free_port(), out), nprocs=world, start_method="spawn", join=True)
+    for rank in range(world):
+        slowest, value = out[rank]
+        assert slowest == 5.0
+        assert value == pytest.approx(5.0 / 8)
+
+
+def test_single_rank_needs_no_process_group():
+    import bench
+
+    assert bench.ranks_max(2.5, 1, "cpu") == 2.5
+    assert bench.job_seconds_per_build(6.0, 3, 1) == pytest.approx(2.0)
+
+
+def test_reference_arm_prints_only_on_rank_zero():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2"],
+                       env=env, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0
+    assert r.stdout.strip() == ""
