@@ -239,6 +239,55 @@ mgw_status mgw_sigma_moments_batched(mgw_handle* h, const mgw_options* o, int ns
                                      const mgw_system* sys);
 
 /*
+ * mgw_g0w0_batched -- the whole G0W0 chain for many independent systems:
+ * for each, the response moments (o->screening), the Sigma moments, block
+ * Lanczos of both sectors (Eqs. 9-10) and the QP solve of mgw_qp_solve with
+ * F = diag(eps) (a canonical Hartree-Fock reference, Sigma_inf = 0), zeta = 0
+ * and N = 2 nocc, in o->precision.  Systems are spread, largest first, over
+ * four internal sub-handles, each driven by a host thread of its own (the
+ * Lanczos ranks and the QP's host scalars synchronise), so small systems
+ * and the host-side decisions of one system overlap the others' GPU work;
+ * each system gets exactly the result of the single-system calls.  The
+ * call returns when every system is done.  Not in the paper.
+ *   sys: HOST array; eps [nmo], L [naux][nmo][nmo] device in; eps_qp [nmo]
+ *   device out; mu, nelec, rank_h, rank_p host out.  0 <= nmom_max <= 11.
+ */
+typedef struct {
+  int nocc, nvir, naux;
+  const double* eps;      /* [nmo]              in */
+  const double* L;        /* [naux][nmo][nmo]   in */
+  double* eps_qp;         /* [nmo]              out */
+  double mu, nelec;       /* host out: Aufbau chemical potential and count */
+  int rank_h, rank_p;     /* host out: retained ranks of the two Sigma(0) */
+} mgw_g0w0_system;
+
+mgw_status mgw_g0w0_batched(mgw_handle* h, const mgw_options* o, int nsys, int nmom_max,
+                            mgw_g0w0_system* sys);
+
+/*
+ * mgw_response_moments_batched -- mgw_response_moments for many independent
+ * systems, spread over the same sub-handles and host threads as
+ * mgw_g0w0_batched.  Not in the paper.
+ *   sys: HOST array of device pointers eps_W [nmo], Lov [naux][nocc*nvir] in,
+ *   Wmom [nmom][naux][naux] out.
+ */
+typedef struct {
+  int nocc, nvir, naux;
+  const double* eps_W;
+  const double* Lov;
+  double* Wmom;
+} mgw_response_system;
+
+mgw_status mgw_response_moments_batched(mgw_handle* h, const mgw_options* o, int nsys, int nmom,
+                                        const mgw_response_system* sys);
+
+/*
+ * mgw_sync_status -- wait for everything queued on the handle's stream and
+ * report a CUDA error that any of it raised (MGW_ERR_CUDA), else MGW_OK.
+ */
+mgw_status mgw_sync_status(mgw_handle* h);
+
+/*
  * mgw_fsgw_step -- one outer iteration of Fock self-consistent GW
  * (Algorithm 2, Sec. III F).  In the reference orbital basis of h and L:
  *   1. L' = C^T L C; response moments, Sigma moments and both block-Lanczos

@@ -31,6 +31,9 @@ struct mgw_handle {
   // table, replayed while it is unchanged; a stream of its own to capture on
   void* batched_plan = nullptr;
   void (*batched_plan_free)(void*) = nullptr;
+  // whole-chain batches (batched_chain.cu): sub-handles driven by host threads
+  void* chain_pool = nullptr;
+  void (*chain_pool_free)(void*) = nullptr;
   cudaStream_t capture_stream = nullptr;
   // when set, tensor-core pipelines record wait timeouts here and return
   // without synchronising; whoever set it reads the word once at the end

@@ -441,11 +441,9 @@ mgw_status ozaki_launch(mgw_handle* h, const CUtensorMap& mA, const CUtensorMap&
   if (K >= (1 << 24))  // the exact 128-bit combine of the epilogue needs K < 2^24
     return fail(h, MGW_ERR_UNSUPPORTED, "%s: K = %d too large for the digit-sliced GEMM", what, K);
   auto kern = ozaki_gemm_kernel<ALoad, Epi>;
-  static bool attr = false;
-  if (!attr) {
-    MGW_CUDA(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
-    attr = true;
-  }
+  // once per instantiation (thread-safe static initialisation)
+  static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  MGW_CUDA(h, attr);
   dim3 grid((unsigned)(((N + BN - 1) / BN) * ((M + BM - 1) / BM)), 1, 1);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (h->prof) {

@@ -174,11 +174,9 @@ mgw_status tc_gemm_launch(mgw_handle* h, const CUtensorMap* A, const CUtensorMap
                           int N, int K, const Loader& ld, const Epi& epi, int* dstatus, const char* what) {
   using L = SmemLayout<BN, STAGES>;
   auto kern = tc_gemm_kernel<BN, STAGES, Loader, Epi>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    MGW_CUDA(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes));
-    attr_set = true;
-  }
+  // once per instantiation (thread-safe static initialisation)
+  static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes);
+  MGW_CUDA(h, attr);
   dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM), 1);
   cudaEvent_t ea = nullptr, eb = nullptr;
   if (h->prof) {

@@ -68,6 +68,18 @@ class System(ctypes.Structure):
                 ("sig_part", ctypes.c_void_p)]
 
 
+class G0w0System(ctypes.Structure):
+    _fields_ = [("nocc", ctypes.c_int), ("nvir", ctypes.c_int), ("naux", ctypes.c_int),
+                ("eps", ctypes.c_void_p), ("L", ctypes.c_void_p), ("eps_qp", ctypes.c_void_p),
+                ("mu", ctypes.c_double), ("nelec", ctypes.c_double), ("rank_h", ctypes.c_int),
+                ("rank_p", ctypes.c_int)]
+
+
+class ResponseSystem(ctypes.Structure):
+    _fields_ = [("nocc", ctypes.c_int), ("nvir", ctypes.c_int), ("naux", ctypes.c_int),
+                ("eps_W", ctypes.c_void_p), ("Lov", ctypes.c_void_p), ("Wmom", ctypes.c_void_p)]
+
+
 _lib = None
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -132,6 +144,12 @@ def load(path: str | None = None):
     lib.mgw_fsgw_step.restype = _I
     lib.mgw_hf_core.argtypes = [_P, _I, _I, _I, _P, _P, _P]
     lib.mgw_hf_core.restype = _I
+    lib.mgw_g0w0_batched.argtypes = [_P, _P, _I, _I, ctypes.POINTER(G0w0System)]
+    lib.mgw_g0w0_batched.restype = _I
+    lib.mgw_response_moments_batched.argtypes = [_P, _P, _I, _I, ctypes.POINTER(ResponseSystem)]
+    lib.mgw_response_moments_batched.restype = _I
+    lib.mgw_sync_status.argtypes = [_P]
+    lib.mgw_sync_status.restype = _I
     for name, args in _SIGS.items():
         fn = getattr(lib, name)
         fn.argtypes = [_P] + args
@@ -235,6 +253,37 @@ class Handle:
             outs.append((sh, sp))
         self._check(self._lib.mgw_sigma_moments_batched(self._h, ctypes.byref(opts), len(systems), nmom, arr))
         return outs
+
+    def mgw_g0w0_batched(self, opts: Options, nmom_max, systems):
+        """systems: list of dicts with nocc, nvir, naux, eps, L (device tensors);
+        returns per system a dict with eps_qp, mu, nelec, rank_h, rank_p."""
+        arr = (G0w0System * len(systems))()
+        outs = []
+        for i, sy in enumerate(systems):
+            nmo = sy["nocc"] + sy["nvir"]
+            e = torch.empty((nmo,), dtype=torch.float64, device=sy["L"].device)
+            arr[i] = G0w0System(sy["nocc"], sy["nvir"], sy["naux"], _ptr(sy["eps"], (nmo,), "eps"),
+                                _ptr(sy["L"], (sy["naux"], nmo, nmo), "L"), _ptr(e), 0.0, 0.0, 0, 0)
+            outs.append(e)
+        self._check(self._lib.mgw_g0w0_batched(self._h, ctypes.byref(opts), len(systems), nmom_max, arr))
+        return [dict(eps_qp=e, mu=arr[i].mu, nelec=arr[i].nelec, rank_h=arr[i].rank_h, rank_p=arr[i].rank_p)
+                for i, e in enumerate(outs)]
+
+    def mgw_response_moments_batched(self, opts: Options, nmom, systems):
+        """systems: list of dicts with nocc, nvir, naux, eps, Lov; returns W per system."""
+        arr = (ResponseSystem * len(systems))()
+        outs = []
+        for i, sy in enumerate(systems):
+            nmo, ov = sy["nocc"] + sy["nvir"], sy["nocc"] * sy["nvir"]
+            W = torch.empty((nmom, sy["naux"], sy["naux"]), dtype=torch.float64, device=sy["Lov"].device)
+            arr[i] = ResponseSystem(sy["nocc"], sy["nvir"], sy["naux"], _ptr(sy["eps"], (nmo,), "eps"),
+                                    _ptr(sy["Lov"], (sy["naux"], ov), "Lov"), _ptr(W))
+            outs.append(W)
+        self._check(self._lib.mgw_response_moments_batched(self._h, ctypes.byref(opts), len(systems), nmom, arr))
+        return outs
+
+    def mgw_sync_status(self):
+        self._check(self._lib.mgw_sync_status(self._h))
 
     def mgw_hf_core(self, nocc, eps, L):
         """h = diag(eps) - J[rho_HF] + K[rho_HF]/2 (F[rho_HF] = diag(eps))."""

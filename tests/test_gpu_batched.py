@@ -103,3 +103,33 @@ def test_batched_tensor_core_path_matches_oracle():
                 assert rel(gh[n], rh[n]) < 1e-9, (call, n)
                 assert rel(gp[n], rp[n]) < 1e-9, (call, n)
     h.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp64_tc"])
+def test_g0w0_and_response_batched_match_single_system_calls(precision):
+    """The whole-chain batch (sub-handles on host threads) gives each system
+    the single-system chain's QP energies, Aufbau count and ranks; the batched
+    response moments equal the single-system ones."""
+    from paper_2504_17439_gb300 import build, driver, mgw
+
+    build.build()
+    h = mgw.Handle(0)
+    o = mgw.options(precision=mgw.MGW_FP64 if precision == "fp64" else mgw.MGW_FP64_TC)
+    shapes = mgw_inputs.batch_shapes(7, seed=81, nmo_lo=10, nmo_hi=60, nmom_max=3)
+    systems = []
+    for i, sh in enumerate(shapes):
+        eps = torch.from_numpy(mgw_inputs.orbital_energies(sh.nocc, sh.nvir, 900 + i)).cuda()
+        L = torch.from_numpy(mgw_inputs.df_tensor(sh.naux, sh.nmo, 900 + i) * 2.0).cuda()
+        systems.append(dict(nocc=sh.nocc, nvir=sh.nvir, naux=sh.naux, eps=eps, L=L,
+                            Lov=h.mgw_extract_ov(sh.nocc, sh.nvir, L)))
+    res = h.mgw_g0w0_batched(o, 3, systems)
+    Ws = h.mgw_response_moments_batched(o, 8, systems)
+    h.mgw_sync_status()
+    for sy, r, W in zip(systems, res, Ws):
+        ref = driver.g0w0(h, sy["eps"], sy["L"], sy["nocc"], 3, opts=mgw.options(precision=o.precision))
+        assert r["rank_h"] == ref["hole"][3] and r["rank_p"] == ref["part"][3]
+        assert abs(r["nelec"] - ref["nelec"]) < 1e-9
+        assert float((r["eps_qp"] - ref["eps_qp"]).abs().max()) < 1e-9
+        Wr = h.mgw_response_moments(o, sy["nocc"], sy["nvir"], sy["naux"], 8, sy["eps"], sy["Lov"])
+        assert float((W - Wr).abs().max()) <= 1e-12 * float(Wr.abs().max())
+    h.close()
