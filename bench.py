@@ -439,9 +439,19 @@ def run_batched(args):
             out.append(h.mgw_sigma_moments(otc, sy["nocc"], sy["nvir"], sy["naux"], nmom, sy["eps"], sy["L"], W))
         return out
 
+    from paper_2504_17439_gb300 import driver
+
+    def g0w0_batched_tc():  # the whole chain: moments, Lanczos, QP solve
+        return h.mgw_g0w0_batched(otc, 5, systems)
+
+    def g0w0_sequential_tc():
+        return [driver.g0w0(h, sy["eps"], sy["L"], sy["nocc"], 5, opts=mgw.options(precision=mgw.MGW_FP64_TC))
+                for sy in systems]
+
     res = {}
     for name, fn in (("batched_tc", batched_tc), ("sequential_tc", sequential_tc), ("grouped", grouped),
-                     ("sequential", sequential)):
+                     ("sequential", sequential), ("g0w0_batched_tc", g0w0_batched_tc),
+                     ("g0w0_sequential_tc", g0w0_sequential_tc)):
         for _ in range(args.warmup):
             fn()
         torch.cuda.synchronize()
@@ -464,6 +474,7 @@ def run_batched(args):
             "systems_per_s": {k: len(systems) / v for k, v in res.items()},
             "speedup_vs_sequential_fp64": res["sequential"] / res["batched_tc"],
             "fp64_grouped_graph_vs_sequential_fp64": res["sequential"] / res["grouped"],
+            "g0w0_chain_batched_vs_sequential": res["g0w0_sequential_tc"] / res["g0w0_batched_tc"],
             "max_rel_diff_fp64_grouped_vs_sequential": diff,
             "max_rel_diff_tc_batched_vs_fp64_sequential": diff_tc}
     print(json.dumps(line), flush=True)
