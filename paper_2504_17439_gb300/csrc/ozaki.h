@@ -60,33 +60,40 @@ constexpr int kBand = 8;       // tile rows per band of the launch order (L2 reu
 constexpr int kTileBytes = BM * BK * 2;  // one A digit tile (16 KB)
 constexpr int kTileBytesB = BN * BK * 2; // one B digit tile (12 KB)
 constexpr int kStageBytes = kTileBytes + kTileBytesB;
-constexpr int kSmemBytes = 1024 + kStages * kStageBytes + 256;
+constexpr int kBarBytes = 256;         // mbarriers and the TMEM address
+constexpr int kSmemBytes = 1024 + kStages * kStageBytes + kBarBytes + BN * 4;  // + the tile's column exponents
+static_assert(kSmemBytes <= 232448, "dynamic shared memory above the 227 KB opt-in limit");
 constexpr uint64_t kWaitNs = 2000000000ull;
 
 // W 2^E for a nonzero 64-bit integer W, rounded to the nearest double
-// (ties to even) with integer operations only.
+// (ties to even), subnormal and overflowing results included, with integer
+// operations only.  The significand is taken in units of the result's last
+// place 2^u, u = max(p + E - 52, -1074) for the leading bit p of |W|; adding
+// it to (u + 1074) 2^52 gives the IEEE pattern of normal and subnormal
+// results alike, a rounding carry moving into the exponent field.  There is
+// no FP64 instruction here, not even in an untaken branch: the FP64 pipe of
+// this part runs at a small fraction of the integer rate, and an ldexp
+// fallback made the final combine several times slower than its integer work.
 __device__ __forceinline__ double i64_ldexp(long long W, int E) {
-  const bool neg = W < 0;
-  const unsigned long long M = neg ? 0ull - (unsigned long long)W : (unsigned long long)W;
+  const unsigned long long sign = (unsigned long long)(W < 0) << 63;
+  const unsigned long long M = W < 0 ? 0ull - (unsigned long long)W : (unsigned long long)W;
   const int p = 63 - __clzll((long long)M);
-  unsigned long long mant;
-  int top = p;
-  if (p > 52) {
-    const int r = p - 52;
-    mant = M >> r;
-    const unsigned long long rem = M & ((1ull << r) - 1), half = 1ull << (r - 1);
-    if (rem > half || (rem == half && (mant & 1ull))) ++mant;
-    if (mant >> 53) {
-      mant >>= 1;
-      ++top;
-    }
+  const int u = max(p + E - 52, -1074);
+  const int r = u - E;  // right shift of M onto the last place, >= p - 52 >= -52
+  unsigned long long q;
+  if (r <= 0) {
+    q = M << -r;
+  } else if (r >= 64) {
+    q = 0;  // |W| <= 2^63: at most half the last place, ties to the even 0
   } else {
-    mant = M << (52 - p);
+    q = M >> r;
+    const unsigned long long rem = M & ((1ull << r) - 1), half = 1ull << (r - 1);
+    if (rem > half || (rem == half && (q & 1ull))) ++q;
   }
-  const int be = top + E + 1023;
-  if (be < 1 || be > 2046) return ldexp(neg ? -(double)M : (double)M, E);  // outside the normal range
-  return __longlong_as_double(
-      (long long)(((unsigned long long)neg << 63) | ((unsigned long long)be << 52) | (mant & ((1ull << 52) - 1))));
+  // |E| < 2400 for exponents of FP64 operands, so u + 1074 < 4096 fits the shift
+  unsigned long long bits = ((unsigned long long)(u + 1074) << 52) + q;
+  if ((bits >> 52) >= 2047) bits = 0x7FF0000000000000ull;  // overflow to infinity
+  return __longlong_as_double((long long)(bits | sign));
 }
 
 // (acc 2^-24 + a67 2^-40 + v) 2^E as a double, FP64 units untouched.
@@ -194,6 +201,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
   uint64_t* accf = empty + kGroups;  // [2] accumulator b ready for the epilogue
   uint64_t* acce = accf + 2;         // [2] accumulator b drained by the epilogue
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
+  int* col_exp = reinterpret_cast<int*>(smem + kStages * kStageBytes + kBarBytes);  // [BN]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // banded tile order: kBand tile rows sweep the tile columns together, so
@@ -311,6 +319,14 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
     for (int j = 0; j < kCols; ++j) acc[j] = 0;
     const int row = m0 + row_local;
     const int ei = row < M ? ea[row] : 0;
+    // the tile's column exponents, read once here: a global load per element
+    // in the final combine would wait on L2 while the other SMs stream digit
+    // tiles through it
+    {
+      const int te = threadIdx.x - 32 * kEpiWarp0;
+      if (te < BN) col_exp[te] = n0 + te < N ? eb[n0 + te] : 0;
+      named_bar(1, 256);
+    }
     // this thread's 48 elements of the level-6..7 integer accumulator: 96 words
     const uint32_t tw = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(2 * BN) + (uint32_t)(2 * col_base);
     {
@@ -373,21 +389,28 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
         const int nchunks = (sched.kb_total + chunk_of_level(l) / BK - 1) / (chunk_of_level(l) / BK);
         if (++chunk_idx == nchunks) { chunk_idx = 0; ++l_of_phase; }
       } else {
-        // last phase: value = 2^(e_i + f_j - 16) (acc 2^-24 + acc67 2^-40 + low), kept in acc's registers
-#pragma unroll
+        // last phase: value = 2^(e_i + f_j - 16) (acc 2^-24 + acc67 2^-40 + low).
+        // This runs once per tile, long after the code was last fetched, so the
+        // loop over groups of 8 elements stays rolled: fully unrolled, 48
+        // inlined combines made it wait on instruction fetches from L2.  acc[]
+        // rotates by 8 per group, so every group reads acc[0..7] (register
+        // indices stay static) and the results end in element order.
+#pragma unroll 1
         for (int c = 0; c < kCols / 8; ++c) {
-          float v[16];
-          tmem_ld16(ta + (c >> 1) * 16, v);
+          float v[8];
+          tmem_ld8(ta + c * 8, v);
           uint32_t w[16];
           tmem_ld16u(tw + 16 * c, w);
+          long long r[8];
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
-            const int e = c * 8 + j;
-            const int col = n0 + col_base + e;
-            const int fj = col < N ? eb[col] : 0;
             const long long a67 = (long long)(((unsigned long long)w[2 * j + 1] << 32) | w[2 * j]);
-            acc[e] = __double_as_longlong(combine_parts(acc[e], a67, v[(c & 1) * 8 + j], ei + fj - 16));
+            r[j] = __double_as_longlong(combine_parts(acc[j], a67, v[j], ei + col_exp[col_base + c * 8 + j] - 16));
           }
+#pragma unroll
+          for (int j = 0; j < kCols - 8; ++j) acc[j] = acc[j + 8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[kCols - 8 + j] = r[j];
         }
       }
       tc_fence_before();

@@ -49,18 +49,23 @@ struct EpiBinomialTC {
   __device__ __forceinline__ void operator()(int row_local, int col_base, int m0, int n0, int, int N,
                                              const long long (&v)[oz::kCols], double* smem) const {
     constexpr int LD = oz::BN + 1;
+    const int tid = threadIdx.x - 32 * oz::kEpiWarp0;
+    const int pairs = PB * oz::BN;
+    // eps_x of this thread's next (pl, column) pair, loaded one pair ahead
+    auto eps_of = [&](int pi) { const long n = n0 + pi % oz::BN; return n < N ? eps[n / nmo] : 0.0; };
+    double e_next = tid < pairs ? eps_of(tid) : 0.0;
 #pragma unroll
     for (int j = 0; j < oz::kCols; ++j) smem[row_local * LD + col_base + j] = __longlong_as_double(v[j]);
     tc::named_bar(1, 256);
     const long g = m0 / 128;
-    const int tid = threadIdx.x - 32 * oz::kEpiWarp0;
-    const int pairs = PB * oz::BN;
     for (int pi = tid; pi < pairs; pi += 256) {
+      const double e_cur = e_next;
+      if (pi + 256 < pairs) e_next = eps_of(pi + 256);
       const int pl = pi / oz::BN, col = pi % oz::BN;
       const long P = g * PB + pl;
       const long n = n0 + col;
       if (P >= naux || n >= N) continue;
-      const double es = sgn * eps[n / nmo];
+      const double es = sgn * e_cur;
       double a[NMAX];
 #pragma unroll
       for (int t = 0; t < NMAX; ++t) a[t] = t < nmom ? smem[(t * PB + pl) * LD + col] : 0.0;
