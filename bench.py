@@ -28,6 +28,7 @@ total builds, scaling "weak".
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -48,6 +49,33 @@ WORKLOAD = "g0w0-nmo400-naux1600"
 METRIC = "sigma_moment_build_s"
 FP64_PEAK_GFLOPS = 1250.0  # nominal GB300 FP64 (DFMA) rate; the ALU bound of the FP64 path
 DIGIT_PRODUCTS = 28        # BF16 digit products per FP64-accurate tensor-core product (7 digits, levels <= 8)
+
+# DRAM bytes per launch of the dominant kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum averaged over the 32 launches of one step), from one
+# ncu pass over `python bench.py --steps 1 --warmup 1 --no-cpu-baseline
+# --no-compare` with `--kernel-name-base demangled -k regex:EpiBinomialTC -c 32`.
+# A counter belongs to the kernel it was taken on: the entry holds the SHA-256
+# of the sources that define that kernel, and a changed source reports null.
+TRAFFIC_SOURCES = ("ozaki.h", "ozaki.cu", "tc_common.h", "sigma.cu")
+TRAFFIC = {
+    ("g0w0-nmo400-naux1600", "fp64_tc"): ("abd46ee385b2c9b4a8ec67ee0b543e0f58af5de516511dd03c654e63ac259b75", 4.5949e9),
+}
+
+
+def kernel_sources_sha256():
+    csrc = os.path.join(ROOT, "paper_2504_17439_gb300", "csrc")
+    digest = hashlib.sha256()
+    for name in TRAFFIC_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as f:
+            digest.update(f.read())
+    return digest.hexdigest()
+
+
+def measured_traffic(workload, precision):
+    entry = TRAFFIC.get((workload, precision))
+    if entry is None or entry[0] != kernel_sources_sha256():
+        return None
+    return entry[1]
 
 
 def measured_peaks():
@@ -309,7 +337,8 @@ def run_gpu(args):
     if tc:
         peak = peaks.get("bf16_tflops_sustained", 1700.0) * 1e3
         roofline = {"kernel": ykern, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
-                    "frac": achieved / peak if achieved else None, "traffic": None,
+                    "frac": achieved / peak if achieved else None,
+                    "traffic": measured_traffic(args.workload, args.precision),
                     "fp64_equivalent_gflops": achieved / DIGIT_PRODUCTS if achieved else None,
                     "peak_source": "bf16_tflops_sustained of measured (MEASURED_PEAKS.json)" if peaks
                     else "sustained bf16 of fallback"}

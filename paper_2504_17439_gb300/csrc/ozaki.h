@@ -39,6 +39,8 @@
 #include "tc_common.h"
 #include "mgw_internal.h"
 
+#include <algorithm>
+
 namespace mgw {
 namespace oz {
 
@@ -56,7 +58,8 @@ constexpr int kStages = 8;     // stage slots (one K block of one digit product 
 constexpr int kGroup = 2;      // slots per full/empty barrier
 constexpr int kGroups = kStages / kGroup;
 static_assert(kGroups % kProducers == 0, "each barrier group has one producer warp");
-constexpr int kBand = 8;       // tile rows per band of the launch order (L2 reuse)
+constexpr int kBand = 8;       // tile rows per row band of the launch order (L2 reuse)
+constexpr int kBandN = 19;     // tile columns per column band: 8 x 19 = 152 CTAs, one wave
 constexpr int kTileBytes = BM * BK * 2;  // one A digit tile (16 KB)
 constexpr int kTileBytesB = BN * BK * 2; // one B digit tile (12 KB)
 constexpr int kStageBytes = kTileBytes + kTileBytesB;
@@ -191,7 +194,8 @@ struct ARowsPlain {
 template <class ALoad, class Epi>
 __global__ void __launch_bounds__(kThreads, 1)
 ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
-                  const int* __restrict__ ea, const int* __restrict__ eb, int M, int N, int K, ALoad al, Epi epi,
+                  const int* __restrict__ ea, const int* __restrict__ eb, int M, int N, int K, int col_band,
+                  int ksplit, ALoad al, Epi epi,
                   int* status) {
   using namespace tc;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -204,14 +208,33 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
   int* col_exp = reinterpret_cast<int*>(smem + kStages * kStageBytes + kBarBytes);  // [BN]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // banded tile order: kBand tile rows sweep the tile columns together, so
-  // the CTAs resident at one time share their A and B digit tiles in L2
+  // banded tile order.  Row bands: kBand tile rows sweep the tile columns
+  // together, the band's A digit tiles stay in L2 and B streams once per band.
+  // Column bands: kBandN tile columns sweep the tile rows, every wave re-touches
+  // the band's B tiles (they stay in L2) and A streams once per band.
   const int MT = (M + BM - 1) / BM, NT = (N + BN - 1) / BN;
-  const int band = (int)(blockIdx.x / (unsigned)(kBand * NT));
-  const int rem = (int)(blockIdx.x % (unsigned)(kBand * NT));
-  const int bh = min(kBand, MT - band * kBand);
-  const int m0 = (band * kBand + rem % bh) * BM, n0 = (rem / bh) * BN;
-  const Schedule sched(K);
+  int mt, nt;
+  if (col_band) {
+    const int band = (int)(blockIdx.x / (unsigned)(kBandN * MT));
+    const int rem = (int)(blockIdx.x % (unsigned)(kBandN * MT));
+    const int bw = min(kBandN, NT - band * kBandN);
+    nt = band * kBandN + rem % bw;
+    mt = rem / bw;
+  } else {
+    const int band = (int)(blockIdx.x / (unsigned)(kBand * NT));
+    const int rem = (int)(blockIdx.x % (unsigned)(kBand * NT));
+    const int bh = min(kBand, MT - band * kBand);
+    mt = band * kBand + rem % bh;
+    nt = rem / bh;
+  }
+  const int m0 = mt * BM, n0 = nt * BN;
+  // tiles the epilogue does not need (the lower triangle of a symmetric
+  // result) end here, before any barrier, TMEM or shared-memory set-up
+  if (epi.skip_tile(m0, n0, M, N)) return;
+  // split z = blockIdx.y covers k in [k0, k0 + ksplit); its partial result
+  // goes where the epilogue puts split z
+  const int k0 = (int)blockIdx.y * ksplit;
+  const Schedule sched(min(ksplit, K - k0));
 
   if (threadIdx.x == 0) {
     for (int g = 0; g < kGroups; ++g) {
@@ -259,8 +282,8 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
           if (it % kGroup == 0)
             mbar_arrive_expect_tx(&full[gs], (uint32_t)(min(kGroup, total - g * kGroup) * kStageBytes));
           uint8_t* sa = smem + (it % kStages) * kStageBytes;
-          al.load(&mA, sa, &full[gs], kb * BK, m0, s - 1);
-          tma_load_3d(sa + kTileBytes, &mB, &full[gs], kb * BK, n0, u - 1);
+          al.load(&mA, sa, &full[gs], k0 + kb * BK, m0, s - 1);
+          tma_load_3d(sa + kTileBytes, &mB, &full[gs], k0 + kb * BK, n0, u - 1);
         }
         __syncwarp();
       }
@@ -457,24 +480,44 @@ void place_sliced(double* mem, long rows, long K, Sliced& s);
 // 3D tensor map over digits: (k, row, digit), box (64, box_rows, 1)
 mgw_status digit_map(mgw_handle* h, CUtensorMap* map, const Sliced& s, int box_rows);
 
+// K blocks per split and the number of splits a launch with nsplit requested
+// makes (each split a whole number of BK blocks, none empty)
+inline long split_kblocks(long K, int nsplit) {
+  const long kb = (K + BK - 1) / BK;
+  const long ns = std::max(1L, std::min<long>(nsplit, kb));
+  return (kb + ns - 1) / ns;
+}
+inline int split_count(long K, int nsplit) {
+  const long kb = (K + BK - 1) / BK, kbs = split_kblocks(K, nsplit);
+  return (int)((kb + kbs - 1) / kbs);
+}
+
 template <class ALoad, class Epi>
 mgw_status ozaki_launch(mgw_handle* h, const CUtensorMap& mA, const CUtensorMap& mB, const int* ea,
                         const int* eb, int M, int N, int K, const ALoad& al, const Epi& epi, int* dstatus,
-                        const char* what) {
+                        const char* what, int nsplit = 1) {
   if (K >= (1 << 24))  // the exact 128-bit combine of the epilogue needs K < 2^24
     return fail(h, MGW_ERR_UNSUPPORTED, "%s: K = %d too large for the digit-sliced GEMM", what, K);
   auto kern = ozaki_gemm_kernel<ALoad, Epi>;
   // once per instantiation (thread-safe static initialisation)
   static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
   MGW_CUDA(h, attr);
-  dim3 grid((unsigned)(((N + BN - 1) / BN) * ((M + BM - 1) / BM)), 1, 1);
+  const long MT = (M + BM - 1) / BM, NT = (N + BN - 1) / BN;
+  const int ksplit = (int)(split_kblocks(K, nsplit) * BK);
+  dim3 grid((unsigned)(MT * NT), (unsigned)split_count(K, nsplit), 1);
+  // launch order with the smaller estimate of operand rows fetched from DRAM:
+  // the resident operand once, the streamed one once per band
+  const double rows_a = (double)MT * BM, rows_b = (double)NT * BN;
+  const double by_rows = rows_a + (double)((MT + kBand - 1) / kBand) * rows_b;
+  const double by_cols = (double)((NT + kBandN - 1) / kBandN) * rows_a + rows_b;
+  const int col_band = by_cols < by_rows ? 1 : 0;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (h->prof) {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, h->stream);
   }
-  kern<<<grid, kThreads, kSmemBytes, h->stream>>>(mA, mB, ea, eb, M, N, K, al, epi, dstatus);
+  kern<<<grid, kThreads, kSmemBytes, h->stream>>>(mA, mB, ea, eb, M, N, K, col_band, ksplit, al, epi, dstatus);
   mgw_status st = check_launch(h, what);
   if (h->prof) {
     cudaEventRecord(e1, h->stream);
@@ -493,6 +536,7 @@ namespace oz {
 template <class F>
 struct EpiElem {
   F f;
+  __device__ bool skip_tile(int m0, int n0, int M, int N) const { return f.skip_tile(m0, n0, M, N); }
   __device__ void operator()(int row_local, int col_base, int m0, int n0, int M, int N,
                              const long long (&v)[kCols], double*) const {
     const int row = m0 + row_local;
@@ -508,6 +552,7 @@ struct EpiElem {
 
 struct FStore {  // C[row][col] = alpha v + beta C
   double* C; long ldc; double alpha, beta;
+  __device__ bool skip_tile(int, int, int, int) const { return false; }
   __device__ void operator()(int r, int c, double v) const {
     double* q = C + (long)r * ldc + c;
     *q = beta == 0.0 ? alpha * v : alpha * v + beta * *q;
@@ -515,17 +560,34 @@ struct FStore {  // C[row][col] = alpha v + beta C
 };
 struct FDiagUpdate {  // T[row][col] = T d[col] + alpha v
   double* T; long ldt; const double* d; double alpha;
+  __device__ bool skip_tile(int, int, int, int) const { return false; }
   __device__ void operator()(int r, int c, double v) const {
     double* q = T + (long)r * ldt + c;
     *q = *q * d[c] + alpha * v;
   }
 };
-struct FSigmaN {  // column (n, q): Sigma(n)[row][q] (+)= v
-  double* sig; int nmo; double beta;
+// Sigma(n) = A B^T with rows p and columns (n, q): a symmetric result in (p, q).
+// Elements with p <= q write (p, q) and (q, p); the rest are dropped, and a
+// tile whose every column has q below its first row is skipped outright (the
+// upper element of each pair lies in a kept tile).  Split z of a K-split
+// launch writes the z-th buffer, split_stride doubles apart.
+__host__ __device__ inline bool sigma_tile_lower(int m0, int n0, int N, int nmo) {
+  const int c1 = (n0 + BN < N ? n0 + BN : N) - 1;
+  return n0 / nmo == c1 / nmo && c1 % nmo < m0;
+}
+struct FSigmaN {
+  double* sig; int nmo; double beta; long split_stride;
+  __device__ bool skip_tile(int m0, int n0, int, int N) const { return sigma_tile_lower(m0, n0, N, nmo); }
   __device__ void operator()(int r, int c, double v) const {
     const int n = c / nmo, q = c % nmo;
-    double* p = sig + ((long)n * nmo + r) * nmo + q;
+    if (r > q) return;
+    double* base = sig + (long)blockIdx.y * split_stride + (long)n * nmo * nmo;
+    double* p = base + (long)r * nmo + q;
     *p = beta == 0.0 ? v : v + *p;
+    if (r != q) {
+      double* t = base + (long)q * nmo + r;
+      *t = beta == 0.0 ? v : v + *t;
+    }
   }
 };
 

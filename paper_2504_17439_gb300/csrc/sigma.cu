@@ -46,6 +46,7 @@ struct EpiBinomialTC {
   int nmom, PB, naux, nmo;
   long ncol;
   double sgn;
+  __device__ bool skip_tile(int, int, int, int) const { return false; }
   __device__ __forceinline__ void operator()(int row_local, int col_base, int m0, int n0, int, int N,
                                              const long long (&v)[oz::kCols], double* smem) const {
     constexpr int LD = oz::BN + 1;
@@ -141,6 +142,29 @@ struct EpiBinomial {
   }
 };
 
+// K splits of the tensor-core GEMM2 (rows p, columns (n, q), K = nx naux):
+// its kept tiles (upper triangle) times the splits should fill whole waves of
+// one CTA per SM, and every CTA also pays a fixed set-up and final combine of
+// about 3 K blocks' worth of MMA time.  Minimises waves x (K blocks per split + 3).
+static int gemm2_splits(int nmo, int nmom, long K2, int sms) {
+  const int MT = (nmo + oz::BM - 1) / oz::BM;
+  const int N = nmom * nmo, NT = (N + oz::BN - 1) / oz::BN;
+  long kept = 0;
+  for (int mt = 0; mt < MT; ++mt)
+    for (int nt = 0; nt < NT; ++nt) kept += oz::sigma_tile_lower(mt * oz::BM, nt * oz::BN, N, nmo) ? 0 : 1;
+  int best = 1;
+  double best_cost = 0.0;
+  for (int s = 1; s <= 16; ++s) {
+    const long waves = (kept * oz::split_count(K2, s) + sms - 1) / sms;
+    const double cost = (double)waves * ((double)oz::split_kblocks(K2, s) + 3.0);
+    if (s == 1 || cost < best_cost) {
+      best = s;
+      best_cost = cost;
+    }
+  }
+  return best;
+}
+
 // sig[i] = (accumulate ? sig[i] : 0) + sum_s part[s * count + i]
 __global__ void k_reduce_splits(long count, int nsplit, const double* part, double* sig, int accumulate) {
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x) {
@@ -183,6 +207,11 @@ extern "C" mgw_status mgw_sigma_moments(mgw_handle* h, const mgw_options* o, int
   const long tiles2 = ((nmo + 63) / 64) * ((nmo + 63) / 64 + 1) / 2;
   int nsplit = (int)std::max(1L, std::min(16L, (152L * 8 + tiles2 * nmom - 1) / (tiles2 * nmom)));
   const long n2 = (long)nmo * nmo;
+  // the tensor-core GEMM2 keeps one partial Sigma per K split (sized for the
+  // largest chunk, whose K is the largest)
+  int sms = 152;
+  MGW_CUDA(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+  const int nsplit_tc = tc ? oz::split_count((long)xc * naux, gemm2_splits(nmo, nmom, (long)xc * naux, sms)) : 1;
 
   // tensor-core Y stage: grouped W digits (once) and per-chunk L digits
   const int PBt = std::max(1, 128 / nmom);
@@ -191,7 +220,7 @@ extern "C" mgw_status mgw_sigma_moments(mgw_handle* h, const mgw_options* o, int
   double *Z = nullptr, *part = nullptr, *wdig = nullptr, *ldig = nullptr, *st = nullptr;
   double *adig = nullptr, *zdig = nullptr;
   ar.add(&Z, (size_t)nmom * naux * xc * nmo);
-  ar.add(&part, (size_t)nsplit * nmom * n2);
+  ar.add(&part, (size_t)std::max(nsplit, nsplit_tc) * nmom * n2);
   if (tc) {
     ar.add(&wdig, oz::sliced_doubles(ngroups_t * 128, naux));
     ar.add(&ldig, oz::sliced_doubles((long)xc * nmo, naux));
@@ -263,9 +292,23 @@ extern "C" mgw_status mgw_sigma_moments(mgw_handle* h, const mgw_options* o, int
         CUtensorMap ma2, mz2;
         MGW_TRY(oz::digit_map(h, &ma2, sa2, oz::BM));
         MGW_TRY(oz::digit_map(h, &mz2, sz2, oz::BN));
-        MGW_TRY((oz::ozaki_launch(h, ma2, mz2, sa2.exps, sz2.exps, nmo, nmom * nmo, (int)K2, oz::ARowsPlain{},
-                                  oz::EpiElem<oz::FSigmaN>{oz::FSigmaN{sig, nmo, first ? 0.0 : 1.0}}, dstatus,
-                                  "sigma_gemm2_tc")));
+        // upper-triangle tiles only, split along K into partial sums (one
+        // buffer per split, summed into Sigma by k_reduce_splits)
+        const int ns2 = std::min(nsplit_tc, gemm2_splits(nmo, nmom, K2, sms));
+        const int nz = oz::split_count(K2, ns2);
+        if (nz == 1) {
+          MGW_TRY((oz::ozaki_launch(h, ma2, mz2, sa2.exps, sz2.exps, nmo, nmom * nmo, (int)K2, oz::ARowsPlain{},
+                                    oz::EpiElem<oz::FSigmaN>{oz::FSigmaN{sig, nmo, first ? 0.0 : 1.0, 0}},
+                                    dstatus, "sigma_gemm2_tc")));
+        } else {
+          MGW_TRY((oz::ozaki_launch(h, ma2, mz2, sa2.exps, sz2.exps, nmo, nmom * nmo, (int)K2, oz::ARowsPlain{},
+                                    oz::EpiElem<oz::FSigmaN>{oz::FSigmaN{part, nmo, 0.0, (long)nmom * n2}},
+                                    dstatus, "sigma_gemm2_tc", ns2)));
+          const long cnt = (long)nmom * n2;
+          k_reduce_splits<<<(unsigned)std::min<long>((cnt + 255) / 256, 152L * 16), 256, 0, h->stream>>>(
+              cnt, nz, part, sig, first ? 0 : 1);
+          MGW_TRY(check_launch(h, "reduce_splits"));
+        }
         first = false;
         continue;
       }

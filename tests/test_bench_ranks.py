@@ -56,3 +56,15 @@ def test_reference_arm_prints_only_on_rank_zero():
                        env=env, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0
     assert r.stdout.strip() == ""
+
+
+def test_traffic_reported_only_for_the_sources_it_was_measured_on(monkeypatch):
+    """The roofline's DRAM traffic is an ncu counter of one kernel build: a
+    recorded value whose source hash no longer matches reads as null."""
+    import bench
+
+    sha = bench.kernel_sources_sha256()
+    monkeypatch.setattr(bench, "TRAFFIC", {("w", "p"): (sha, 1.5e9), ("w", "q"): ("0" * 64, 2.5e9)})
+    assert bench.measured_traffic("w", "p") == 1.5e9
+    assert bench.measured_traffic("w", "q") is None  # kernel changed since the capture
+    assert bench.measured_traffic("other", "p") is None
