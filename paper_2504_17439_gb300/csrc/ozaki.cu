@@ -218,6 +218,21 @@ size_t sliced_doubles(long rows, long K) {
   return (size_t)((kSlices * rows * ld * 2 + 7) / 8) + (size_t)((rows * 4 + 7) / 8) + (size_t)rows + 64;
 }
 
+__global__ void k_sum_splits(long count, int nsplit, const double* __restrict__ part, double* out,
+                             int accumulate) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x) {
+    double acc = accumulate ? out[i] : 0.0;
+    for (int z = 0; z < nsplit; ++z) acc += part[(long)z * count + i];
+    out[i] = acc;
+  }
+}
+
+mgw_status reduce_splits(mgw_handle* h, long count, int nsplit, const double* part, double* out, int accumulate) {
+  k_sum_splits<<<(unsigned)std::min<long>((count + 255) / 256, 152L * 16), 256, 0, h->stream>>>(count, nsplit, part,
+                                                                                               out, accumulate);
+  return check_launch(h, "reduce_splits");
+}
+
 struct EpiStoreRows {
   double* C;
   long ldc;

@@ -491,6 +491,25 @@ inline int split_count(long K, int nsplit) {
   const long kb = (K + BK - 1) / BK, kbs = split_kblocks(K, nsplit);
   return (int)((kb + kbs - 1) / kbs);
 }
+// Splits to request for a launch of `kept` tiles: kept tiles x splits should
+// fill whole waves of one CTA per SM, and every CTA also pays a fixed set-up
+// and final combine of about 3 K blocks' worth of MMA time.  Minimises
+// waves x (K blocks per split + 3) over 1..16 splits.
+inline int best_split(long kept, long K, int sms) {
+  int best = 1;
+  double best_cost = 0.0;
+  for (int s = 1; s <= 16; ++s) {
+    const long waves = (kept * split_count(K, s) + sms - 1) / sms;
+    const double cost = (double)waves * ((double)split_kblocks(K, s) + 3.0);
+    if (s == 1 || cost < best_cost) {
+      best = s;
+      best_cost = cost;
+    }
+  }
+  return best;
+}
+// sum of the split buffers: out[i] = (accumulate ? out[i] : 0) + sum_z part[z count + i]
+mgw_status reduce_splits(mgw_handle* h, long count, int nsplit, const double* part, double* out, int accumulate);
 
 template <class ALoad, class Epi>
 mgw_status ozaki_launch(mgw_handle* h, const CUtensorMap& mA, const CUtensorMap& mB, const int* ea,
@@ -556,6 +575,23 @@ struct FStore {  // C[row][col] = alpha v + beta C
   __device__ void operator()(int r, int c, double v) const {
     double* q = C + (long)r * ldc + c;
     *q = beta == 0.0 ? alpha * v : alpha * v + beta * *q;
+  }
+};
+// C = A B^T known to be symmetric (M == N): elements with row <= col write
+// (row, col) and (col, row), the rest are dropped, and tiles wholly below the
+// diagonal are skipped (the upper element of each pair lies in a kept tile).
+// Split z of a K-split launch writes the z-th buffer, split_stride apart.
+__host__ __device__ inline bool sym_tile_lower(int m0, int n0, int N) {
+  return (n0 + BN < N ? n0 + BN : N) - 1 < m0;
+}
+struct FStoreSym {
+  double* C; long ldc; long split_stride;
+  __device__ bool skip_tile(int m0, int n0, int, int N) const { return sym_tile_lower(m0, n0, N); }
+  __device__ void operator()(int r, int c, double v) const {
+    if (r > c) return;
+    double* base = C + (long)blockIdx.y * split_stride;
+    base[(long)r * ldc + c] = v;
+    if (r != c) base[(long)c * ldc + r] = v;
   }
 };
 struct FDiagUpdate {  // T[row][col] = T d[col] + alpha v

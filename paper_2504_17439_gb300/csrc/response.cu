@@ -252,12 +252,24 @@ extern "C" mgw_status mgw_response_moments(mgw_handle* h, const mgw_options* o, 
   ar.add(&D, ov);
   ar.add(&T0, tsz);
   ar.add(&mm, 2);
+  // W(t) = T(t) V^T on the tensor cores: symmetric, so upper-triangle tiles
+  // only, with K = ov split so that the kept tiles fill whole waves
+  int w_req = 1, w_nz = 1;
+  double* wpart = nullptr;
   if (use_tc) {  // digit planes: V (rows Q, K = ov), V^T (rows ia, K = naux), T and W(t) per order
+    int sms = 152;
+    MGW_CUDA(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    long kept = 0;
+    for (int m0 = 0; m0 < naux; m0 += oz::BM)
+      for (int n0 = 0; n0 < naux; n0 += oz::BN) kept += oz::sym_tile_lower(m0, n0, naux) ? 0 : 1;
+    w_req = oz::best_split(kept, ov, sms);
+    w_nz = oz::split_count(ov, w_req);
     ar.add(&vd, oz::sliced_doubles(naux, ov));
     ar.add(&vtd, oz::sliced_doubles(ov, naux));
     ar.add(&td, oz::sliced_doubles(naux, ov));
     ar.add(&wd, oz::sliced_doubles(naux, naux));
     ar.add(&st, 1);
+    if (w_nz > 1) ar.add(&wpart, (size_t)w_nz * na2);
   }
   double *ad = nullptr, *bd = nullptr;
   if (rpa_tc) {  // digit planes: V (rows Q, K = ov), A operands, transposed B operands
@@ -293,8 +305,15 @@ extern "C" mgw_status mgw_response_moments(mgw_handle* h, const mgw_options* o, 
     for (int n = 0; n < nmom; ++n) {
       double* Wn = Wmom + (long)n * na2;
       MGW_TRY(oz::slice_rows(h, naux, ov, T0, ov, stt));
-      MGW_TRY((oz::ozaki_launch(h, mt, mv, stt.exps, sv.exps, naux, naux, (int)ov, oz::ARowsPlain{},
-                                oz::EpiElem<oz::FStore>{oz::FStore{Wn, naux, 1.0, 0.0}}, dstatus, "w_gemm_tc")));
+      if (w_nz == 1) {
+        MGW_TRY((oz::ozaki_launch(h, mt, mv, stt.exps, sv.exps, naux, naux, (int)ov, oz::ARowsPlain{},
+                                  oz::EpiElem<oz::FStoreSym>{oz::FStoreSym{Wn, naux, 0}}, dstatus, "w_gemm_tc")));
+      } else {
+        MGW_TRY((oz::ozaki_launch(h, mt, mv, stt.exps, sv.exps, naux, naux, (int)ov, oz::ARowsPlain{},
+                                  oz::EpiElem<oz::FStoreSym>{oz::FStoreSym{wpart, naux, na2}}, dstatus, "w_gemm_tc",
+                                  w_req)));
+        MGW_TRY(oz::reduce_splits(h, na2, w_nz, wpart, Wn, 0));
+      }
       if (n + 1 < nmom) {
         MGW_TRY(oz::slice_rows(h, naux, naux, Wn, naux, sww));
         MGW_TRY((oz::ozaki_launch(h, mw, mvt, sww.exps, svt.exps, naux, (int)ov, naux, oz::ARowsPlain{},

@@ -142,27 +142,15 @@ struct EpiBinomial {
   }
 };
 
-// K splits of the tensor-core GEMM2 (rows p, columns (n, q), K = nx naux):
-// its kept tiles (upper triangle) times the splits should fill whole waves of
-// one CTA per SM, and every CTA also pays a fixed set-up and final combine of
-// about 3 K blocks' worth of MMA time.  Minimises waves x (K blocks per split + 3).
+// K splits of the tensor-core GEMM2 (rows p, columns (n, q), K = nx naux),
+// chosen for its kept (upper-triangle) tiles
 static int gemm2_splits(int nmo, int nmom, long K2, int sms) {
   const int MT = (nmo + oz::BM - 1) / oz::BM;
   const int N = nmom * nmo, NT = (N + oz::BN - 1) / oz::BN;
   long kept = 0;
   for (int mt = 0; mt < MT; ++mt)
     for (int nt = 0; nt < NT; ++nt) kept += oz::sigma_tile_lower(mt * oz::BM, nt * oz::BN, N, nmo) ? 0 : 1;
-  int best = 1;
-  double best_cost = 0.0;
-  for (int s = 1; s <= 16; ++s) {
-    const long waves = (kept * oz::split_count(K2, s) + sms - 1) / sms;
-    const double cost = (double)waves * ((double)oz::split_kblocks(K2, s) + 3.0);
-    if (s == 1 || cost < best_cost) {
-      best = s;
-      best_cost = cost;
-    }
-  }
-  return best;
+  return oz::best_split(kept, K2, sms);
 }
 
 // sig[i] = (accumulate ? sig[i] : 0) + sum_s part[s * count + i]
