@@ -32,6 +32,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -55,19 +56,28 @@ DIGIT_PRODUCTS = 28        # BF16 digit products per FP64-accurate tensor-core p
 # ncu pass over `python bench.py --steps 1 --warmup 1 --no-cpu-baseline
 # --no-compare` with `--kernel-name-base demangled -k regex:EpiBinomialTC -c 32`.
 # A counter belongs to the kernel it was taken on: the entry holds the SHA-256
-# of the sources that define that kernel, and a changed source reports null.
+# of the code (comments stripped) of the sources that define that kernel, and
+# a changed source reports null.
 TRAFFIC_SOURCES = ("ozaki.h", "ozaki.cu", "tc_common.h", "sigma.cu")
 TRAFFIC = {
-    ("g0w0-nmo400-naux1600", "fp64_tc"): ("0276e8694f15c3929e10217a4a8ec1cf6e9829725be661c08823d39e1652dab9", 4.4259e9),
+    ("g0w0-nmo400-naux1600", "fp64_tc"): ("d5b90ffe5d9c95d8fac62fb2283c3b7e5406fb8f87a664f2792c5a808bfd038f", 4.4259e9),
 }
+
+
+def code_of(source):
+    """C++/CUDA source with comments, trailing blanks and empty lines removed:
+    what the compiler sees, so that editing a comment keeps a measurement."""
+    source = re.sub(r"/\*.*?\*/", "", source, flags=re.S)
+    lines = (re.sub(r"//.*", "", line).rstrip() for line in source.splitlines())
+    return "\n".join(line for line in lines if line)
 
 
 def kernel_sources_sha256():
     csrc = os.path.join(ROOT, "paper_2504_17439_gb300", "csrc")
     digest = hashlib.sha256()
     for name in TRAFFIC_SOURCES:
-        with open(os.path.join(csrc, name), "rb") as f:
-            digest.update(f.read())
+        with open(os.path.join(csrc, name), encoding="utf-8") as f:
+            digest.update(code_of(f.read()).encode())
     return digest.hexdigest()
 
 

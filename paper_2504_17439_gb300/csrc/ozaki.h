@@ -34,6 +34,12 @@
 // Stage slots (one K block of one digit product: 16 KB of A, 12 KB of B)
 // come in groups of two behind one full and one empty barrier, so the MMA
 // thread waits once per eight MMAs.  All waits are time-bounded.
+//
+// Launch: one CTA per output tile in row-band or column-band order (the
+// launcher takes the one fetching fewer operand rows), optionally split
+// along K (blockIdx.y; the epilogue places each split's partial result), and
+// an epilogue may skip tiles it does not need (the lower triangle of a
+// symmetric result) before any set-up.
 #pragma once
 
 #include "tc_common.h"

@@ -68,3 +68,11 @@ def test_traffic_reported_only_for_the_sources_it_was_measured_on(monkeypatch):
     assert bench.measured_traffic("w", "p") == 1.5e9
     assert bench.measured_traffic("w", "q") is None  # kernel changed since the capture
     assert bench.measured_traffic("other", "p") is None
+
+
+def test_traffic_hash_ignores_comments_but_not_code():
+    import bench
+
+    src = "int f(int x) {  // doubles x\n  /* a\n block */ return 2 * x;\n}\n"
+    assert bench.code_of(src) == bench.code_of("int f(int x) {\n\n   return 2 * x;\n}")
+    assert bench.code_of(src) != bench.code_of(src.replace("2 * x", "3 * x"))
