@@ -34,6 +34,13 @@ garbled are listed in the docstrings that use them:
   R7  Aufbau (Eq. 40, Sec. III E): m minimising |N(m) - N_elec| over the
       sorted poles, ties to the smaller m, mu = (E_{m-1} + E_m) / 2.
   R8  Sigma_inf = 0 for a canonical Hartree-Fock reference (Eq. 8).
+  R10 Natural auxiliary functions (Sec. II D, Eq. 14): eps_NAF is an
+      absolute threshold on the eigenvalues of M (kept: lambda > eps_NAF);
+      the pair sum runs over every orbital pair but the virtual-virtual
+      block by default, over all pairs for self-consistent use.
+  R11 Spectral function (Eqs. 11-12): delta of Eq. 11 is a Lorentzian
+      broadening, so A(w) = (1/pi) sum_a weight_a delta / ((w - E_a)^2 +
+      delta^2) with weight_a = sum_p chi_pa^2.
 """
 from __future__ import annotations
 
@@ -352,6 +359,56 @@ def qp_solve(fock, hole, part, nelec: float, zeta: float = 0.0):
     m, mu, n_out = aufbau(E, weight, nelec)
     rho = 2.0 * chi[:, :m] @ chi[:, :m].T
     return dict(E=E, chi=chi, weight=weight, eps_qp=eqp, mu=mu, nelec=n_out, m=m, rho=rho)
+
+
+# ----------------------------------------------------------------------------
+# Spectral function (Eqs. 11-12)
+
+
+def spectral_function(E: np.ndarray, weight: np.ndarray, omega, delta: float) -> np.ndarray:
+    """A(w) of Eq. 12 from the Lehmann form of G in Eq. 11 (reading R11):
+    Im G_pp(w) = -sum_a chi_pa^2 delta / ((w - E_a)^2 + delta^2), so
+    A(w) = (1/pi) sum_a weight_a delta / ((w - E_a)^2 + delta^2)."""
+    w = np.asarray(omega, dtype=float)
+    A = np.zeros(w.shape)
+    for Ea, wa in zip(E, weight):
+        A += wa * delta / ((w - Ea) ** 2 + delta * delta)
+    return A / math.pi
+
+
+# ----------------------------------------------------------------------------
+# Natural auxiliary functions (Sec. II D, Eq. 14)
+
+
+def naf_pairs(nmo: int, nocc: int, pairs: str = "no_vv") -> np.ndarray:
+    """Mask of the orbital pairs (v, w) summed in Eq. 14: all of them, or
+    (the paper's default outside self-consistency) all but virtual-virtual."""
+    mask = np.ones((nmo, nmo), dtype=bool)
+    if pairs == "no_vv":
+        mask[nocc:, nocc:] = False
+    elif pairs != "full":
+        raise ValueError(f"unknown pair space {pairs!r}")
+    return mask
+
+
+def naf_basis(L: np.ndarray, nocc: int, eps_naf: float = 1e-5, pairs: str = "no_vv"):
+    """Eq. 14: M_PQ = sum_vw V_{P,vw} V_{Q,vw} over the chosen pairs; its
+    eigenvectors with eigenvalue above eps_naf (absolute, reading R10) span
+    the natural auxiliary functions.  Returns (U [naux][n_naf], all
+    eigenvalues of M in descending order)."""
+    naux, nmo, _ = L.shape
+    V = L[:, naf_pairs(nmo, nocc, pairs)]
+    M = V @ V.T
+    lam, U = np.linalg.eigh(M)
+    lam, U = lam[::-1], U[:, ::-1]
+    return U[:, lam > eps_naf], lam
+
+
+def naf_compress(L: np.ndarray, nocc: int, eps_naf: float = 1e-5, pairs: str = "no_vv") -> np.ndarray:
+    """The DF tensor in the NAF basis, L'_{A,pq} = sum_P U_{PA} L_{P,pq}
+    (Sec. II D): every later step runs with N_NAF functions for N_aux."""
+    U, _ = naf_basis(L, nocc, eps_naf, pairs)
+    return np.tensordot(U.T, L, axes=1)
 
 
 # ----------------------------------------------------------------------------

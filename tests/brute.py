@@ -159,3 +159,31 @@ def block_tridiagonal(alpha, beta):
             T[(i + 1) * r:(i + 2) * r, i * r:(i + 1) * r] = beta[i]
             T[i * r:(i + 1) * r, (i + 1) * r:(i + 2) * r] = beta[i].T
     return T
+
+
+def spectral_downfolded(H, nmo, omega, delta):
+    """A(w) = -(1/pi) Im tr G(w + i delta) with G of the physical block by
+    downfolding H~ (Eq. 10): G(z) = [z - f - W~ (z - d~)^-1 W~^T]^-1, solved
+    with dense complex linear algebra, no eigendecomposition."""
+    f, Wt, dt = H[:nmo, :nmo], H[:nmo, nmo:], H[nmo:, nmo:]
+    out = []
+    for w in np.atleast_1d(omega):
+        z = complex(w, delta)
+        sig = Wt @ np.linalg.solve(z * np.eye(dt.shape[0]) - dt, Wt.T)
+        G = np.linalg.inv(z * np.eye(nmo) - f - sig)
+        out.append(-np.trace(G).imag / np.pi)
+    return np.array(out)
+
+
+def naf_metric_pairs(L, nocc, pairs):
+    """M_PQ of Eq. 14 by an explicit loop over orbital pairs (v, w), skipping
+    the virtual-virtual block unless pairs == 'full'."""
+    naux, nmo, _ = L.shape
+    M = np.zeros((naux, naux))
+    for v in range(nmo):
+        for w in range(nmo):
+            if pairs != "full" and v >= nocc and w >= nocc:
+                continue
+            col = L[:, v, w]
+            M += np.outer(col, col)
+    return M

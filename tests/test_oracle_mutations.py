@@ -82,6 +82,33 @@ def qp_pin_error(mod):
     return err
 
 
+def spectral_pin_error(mod):
+    eps, L = system()
+    r = orc.g0w0(eps, L, 3, 2)
+    H = orc.upfolded_hamiltonian(np.diag(eps), r["hole"][:3], r["part"][:3])
+    omega = np.linspace(r["E"].min() - 0.5, r["E"].max() + 0.5, 31)
+    got = mod.spectral_function(r["E"], r["weight"], omega, 0.05)
+    return rel(got, brute.spectral_downfolded(H, eps.size, omega, 0.05))
+
+
+def naf_pin_error(mod):
+    # the metric against the explicit pair sum, the truncation error against
+    # the dropped spectrum (Eckart-Young), Sigma(n) unchanged without truncation
+    eps, L = system(naux=14)
+    err = 0.0
+    for pairs in ("no_vv", "full"):
+        _, lam = mod.naf_basis(L, 3, -1.0, pairs)
+        ref = np.sort(np.linalg.eigvalsh(brute.naf_metric_pairs(L, 3, pairs)))[::-1]
+        err = max(err, np.abs(lam - ref).max() / ref.max())
+        V = L[:, orc.naf_pairs(8, 3, pairs)]
+        U, _ = mod.naf_basis(L, 3, 0.5 * (ref[5] + ref[6]), pairs)
+        resid = V - U @ (U.T @ V)
+        err = max(err, abs(np.sum(resid**2) - ref[6:].sum()) / ref.sum())
+    a = orc.g0w0(eps, L, 3, 2)
+    b = orc.g0w0(eps, mod.naf_compress(L, 3, -1.0, "full"), 3, 2)
+    return max(err, max(rel(b["sigma_hole"][n], a["sigma_hole"][n]) for n in range(6)))
+
+
 CASES = [
     # (functions, old, new, pin, screening)
     (["tda_response_moments"], "T * D[None, :] + 2.0 *", "T * D[None, :] + 1.0 *", "sigma", "tda"),
@@ -106,6 +133,13 @@ CASES = [
     (["block_lanczos"], "alpha = [s * a + c * eye for a in alpha]", "alpha = [s * a for a in alpha]", "lanczos", None),
     (["upfolded_hamiltonian"], "H[o + r : o + 2 * r, o : o + r] = beta[i]", "H[o + r : o + 2 * r, o : o + r] = 0.5 * beta[i]", "qp", None),
     (["upfolded_hamiltonian"], "H[:nmo, off : off + r] = coup", "H[:nmo, off : off + r] = coup.T @ coup", "qp", None),
+    (["spectral_function"], "A += wa * delta /", "A += wa * delta * delta /", "spectral", None),
+    (["spectral_function"], "return A / math.pi", "return A / (2.0 * math.pi)", "spectral", None),
+    (["spectral_function"], "((w - Ea) ** 2 + delta * delta)", "((w + Ea) ** 2 + delta * delta)", "spectral", None),
+    (["naf_pairs"], "mask[nocc:, nocc:] = False", "mask[:nocc, :nocc] = False", "naf", None),
+    (["naf_basis"], "return U[:, lam > eps_naf], lam", "return U[:, lam >= -1.0], lam", "naf", None),
+    (["naf_basis"], "lam, U = lam[::-1], U[:, ::-1]", "lam, U = lam[::-1], U", "naf", None),
+    (["naf_compress"], "np.tensordot(U.T, L, axes=1)", "np.tensordot(U.T, L, axes=1) * 1.01", "naf", None),
 ]
 
 
@@ -117,6 +151,10 @@ def test_pins_catch_planted_mistake(case):
         err = sigma_pin_error(mod, screening)
     elif pin == "lanczos":
         err = lanczos_pin_error(mod)
+    elif pin == "spectral":
+        err = spectral_pin_error(mod)
+    elif pin == "naf":
+        err = naf_pin_error(mod)
     else:
         err = qp_pin_error(mod)
     assert not (err < 1e-6), f"planted mistake went unnoticed: {old!r} -> {new!r} (err {err})"
@@ -128,4 +166,6 @@ def test_unmutated_copy_passes_every_pin():
     assert sigma_pin_error(mod, "rpa") < 1e-9
     assert lanczos_pin_error(mod) < 1e-9
     assert qp_pin_error(mod) < 1e-9
+    assert spectral_pin_error(mod) < 1e-10
+    assert naf_pin_error(mod) < 1e-10
     assert math.isfinite(lanczos_pin_error(orc))

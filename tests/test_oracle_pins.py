@@ -305,3 +305,95 @@ def test_tda_rows_subset_matches_full():
     W = orc.tda_response_moments(Lov, D, 6)
     Wr = orc.tda_response_moments(Lov, D, 6, rows=[0, 5, 11])
     assert np.allclose(Wr, W[:, [0, 5, 11]], rtol=1e-13, atol=1e-16)
+
+
+# ------------------------------------------------------- spectral function
+
+
+def _g0w0_poles(nmom_max=2):
+    eps, L = small_system(scale=2.0)
+    r = orc.g0w0(eps, L, 3, nmom_max)
+    H = orc.upfolded_hamiltonian(np.diag(eps), r["hole"][:3], r["part"][:3])
+    return eps.size, H, r["E"], r["weight"]
+
+
+def test_spectral_function_equals_the_downfolded_green_function():
+    # Eq. 12 from the poles of H~ against -Im tr G by downfolding (Eq. 10)
+    nmo, H, E, weight = _g0w0_poles()
+    omega = np.linspace(E.min() - 0.5, E.max() + 0.5, 41)
+    for delta in (0.02, 0.1):
+        got = orc.spectral_function(E, weight, omega, delta)
+        ref = brute.spectral_downfolded(H, nmo, omega, delta)
+        assert rel(got, ref) < 1e-10
+
+
+def test_spectral_function_window_integrals_and_total_weight():
+    # a window integral of A equals the Lorentzian antiderivative summed over
+    # poles, and the weights of H~'s eigenvectors add up to nmo
+    nmo, H, E, weight = _g0w0_poles()
+    assert abs(weight.sum() - nmo) < 1e-10
+    delta = 0.05
+    a, b = E.min() - 0.3, E.min() + 2.0
+    x = np.linspace(a, b, 200001)
+    A = orc.spectral_function(E, weight, x, delta)
+    h = x[1] - x[0]
+    numeric = h * (A.sum() - 0.5 * (A[0] + A[-1]))
+    exact = np.sum(weight * (np.arctan((b - E) / delta) - np.arctan((a - E) / delta))) / math.pi
+    assert abs(numeric - exact) < 1e-6 * exact
+
+
+# ------------------------------------------- natural auxiliary functions
+
+
+@pytest.mark.parametrize("pairs", ["no_vv", "full"])
+def test_naf_metric_matches_the_explicit_pair_sum(pairs):
+    eps, L = small_system(nocc=3, nvir=5, naux=10)
+    _, lam = orc.naf_basis(L, 3, 1e-5, pairs)
+    ref = np.sort(np.linalg.eigvalsh(brute.naf_metric_pairs(L, 3, pairs)))[::-1]
+    assert np.abs(lam - ref).max() < 1e-12 * ref.max()
+
+
+@pytest.mark.parametrize("pairs", ["no_vv", "full"])
+def test_naf_truncation_error_is_the_dropped_spectrum(pairs):
+    # Eckart-Young: projecting the pair columns on the kept eigenvectors of M
+    # leaves a squared Frobenius error equal to the dropped eigenvalues
+    eps, L = small_system(nocc=3, nvir=5, naux=14)
+    V = L[:, orc.naf_pairs(8, 3, pairs)]
+    _, lam = orc.naf_basis(L, 3, -1.0, pairs)
+    thresh = 0.5 * (lam[5] + lam[6])  # keep six
+    U, _ = orc.naf_basis(L, 3, thresh, pairs)
+    assert U.shape[1] == 6
+    resid = V - U @ (U.T @ V)
+    assert abs(np.sum(resid**2) - lam[6:].sum()) < 1e-10 * lam.sum()
+
+
+def test_naf_without_truncation_leaves_the_sigma_moments_unchanged():
+    # keeping every NAF rotates the auxiliary basis; Sigma(n) is invariant
+    eps, L = small_system(nocc=3, nvir=5, naux=12, scale=2.0)
+    Ln = orc.naf_compress(L, 3, -1.0, "full")
+    assert Ln.shape == L.shape
+    a = orc.g0w0(eps, L, 3, 2)
+    b = orc.g0w0(eps, Ln, 3, 2)
+    for n in range(6):
+        assert rel(b["sigma_hole"][n], a["sigma_hole"][n]) < 1e-12
+        assert rel(b["sigma_part"][n], a["sigma_part"][n]) < 1e-12
+
+
+@pytest.mark.parametrize("pairs", ["no_vv", "full"])
+def test_naf_of_an_exactly_low_rank_tensor_keeps_its_rank_and_moments(pairs):
+    # L of rank 5 spread over 12 auxiliary functions: NAF keeps exactly 5 and
+    # the G0W0 moments and QP energies are those of the uncompressed tensor
+    nocc, nmo, naux, r = 3, 8, 12, 5
+    g = np.random.default_rng(11)
+    B = g.standard_normal((r, nmo, nmo))
+    B = 0.1 * (B + B.transpose(0, 2, 1)) / 2
+    L = np.tensordot(g.standard_normal((naux, r)), B, axes=1)
+    eps = mgw_inputs.orbital_energies(nocc, nmo - nocc, 5)
+    Ln = orc.naf_compress(L, nocc, 1e-5, pairs)
+    assert Ln.shape[0] == r
+    a = orc.g0w0(eps, L, nocc, 2)
+    b = orc.g0w0(eps, Ln, nocc, 2)
+    for n in range(6):
+        assert rel(b["sigma_hole"][n], a["sigma_hole"][n]) < 1e-10
+        assert rel(b["sigma_part"][n], a["sigma_part"][n]) < 1e-10
+    assert np.abs(b["eps_qp"] - a["eps_qp"]).max() < 1e-9
