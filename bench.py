@@ -603,6 +603,59 @@ def run_fsgw(args):
     return 0
 
 
+def run_extras(args):
+    """The method's next rows on the bench workload, timed through the C ABI
+    with CUDA events after warm-up: natural-auxiliary-function compression of
+    its DF tensor (Sec. II D, Eq. 14: pair metric and projection as FP64
+    GEMMs, syevd; the call synchronises to return the kept count) and the
+    spectral function (Eq. 12) of 6800 poles, the upfolded Hamiltonian's size
+    at nmo 400 and N = 7, on 20000 frequencies."""
+    import torch
+
+    from paper_2504_17439_gb300 import build, mgw
+
+    build.build()
+    shape, seed = mgw_inputs.workload(args.workload)
+    _, L_np = mgw_inputs.system(shape, seed)
+    L = torch.from_numpy(L_np).cuda()
+    nocc, nmo, naux = shape.nocc, shape.nmo, shape.naux
+    h = mgw.Handle(0, torch.cuda.current_stream())
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(max(1, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3 / args.steps
+
+    eps_naf = 1e-5
+    k = h.mgw_naf_compress(nocc, L, eps_naf, False)[0].shape[0]
+    t_naf = timed(lambda: h.mgw_naf_compress(nocc, L, eps_naf, False))
+    npairs = nocc * nmo + (nmo - nocc) * nocc
+    flops = 2.0 * naux * naux * npairs + 2.0 * k * naux * nmo * nmo
+    g = np.random.default_rng(seed + 7)
+    dim, nw = 6800, 20000
+    E = torch.from_numpy(np.sort(g.uniform(-2.0, 4.0, dim))).cuda()
+    wt = torch.from_numpy(g.uniform(0.0, 1.0, dim)).cuda()
+    omega = torch.linspace(-2.5, 4.5, nw, dtype=torch.float64, device="cuda")
+    t_sp = timed(lambda: h.mgw_spectral_function(E, wt, omega, 0.01))
+    print(json.dumps({
+        "metric": "next_rows", "workload": args.workload, "steps": args.steps, "warmup": args.warmup,
+        "naf": {"seconds": t_naf, "eps_naf": eps_naf, "pairs": "no_vv", "naux": naux, "n_naf": k,
+                "gemm_gflops": flops / t_naf / 1e9, "frac_of_nominal_fp64": flops / t_naf / 1e9 / FP64_PEAK_GFLOPS},
+        "spectral_function": {"seconds": t_sp, "poles": dim, "frequencies": nw,
+                              "lorentzians_per_s": dim * nw / t_sp},
+    }))
+    h.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -618,6 +671,7 @@ def main():
     ap.add_argument("--batched", type=int, default=0, help="uneven batch of N systems instead of one system")
     ap.add_argument("--fsgw", type=int, default=0, help="learned fsGW warm start on N held-out systems")
     ap.add_argument("--fsgw-nmo", default="60,100", help="orbital range of the fsGW systems, lo,hi")
+    ap.add_argument("--extras", action="store_true", help="time the next rows: NAF compression, spectral function")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -625,6 +679,8 @@ def main():
         return run_batched(args)
     if args.fsgw:
         return run_fsgw(args)
+    if args.extras:
+        return run_extras(args)
     return run_gpu(args)
 
 

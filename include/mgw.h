@@ -364,6 +364,38 @@ mgw_status mgw_hf_core(mgw_handle* h, int nocc, int nmo, int naux, const double*
                        double* hcore);
 
 /*
+ * mgw_naf_compress -- natural auxiliary functions (Sec. II D, Eq. 14):
+ * M_PQ = sum_vw L[P][v][w] L[Q][v][w] over every orbital pair (all_pairs != 0)
+ * or over all but the virtual-virtual block (all_pairs == 0, the paper's
+ * default outside self-consistency); the eigenvectors of M with eigenvalue
+ * above eps_naf (an absolute threshold) define
+ *   L_naf[A][p][q] = sum_P U[P][A] L[P][p][q],  A = 0..n_naf-1 in descending
+ * eigenvalue order; later calls take n_naf in place of naux.  Each row is
+ * fixed up to its sign (that of the eigenvector).
+ *   L       [naux][nmo][nmo]   in   device, nmo = nocc + nvir
+ *   L_naf   [naux][nmo][nmo]   out  device, rows 0..n_naf-1 written, the rest untouched
+ *   lam     [naux]             out  device, every eigenvalue of M, descending
+ *   n_naf                      out  host (the call synchronises the stream)
+ * M is formed with FP64 GEMMs and diagonalised with cuSOLVER syevd.
+ * Returns MGW_ERR_ARG for bad sizes or null pointers, MGW_ERR_NO_CONV if the
+ * eigensolver does not converge.
+ */
+mgw_status mgw_naf_compress(mgw_handle* h, int nocc, int nvir, int naux, const double* L, double eps_naf,
+                            int all_pairs, double* L_naf, double* lam, int* n_naf);
+
+/*
+ * mgw_spectral_function -- A(w) of Eq. 12 from the poles of H~ (Eq. 11)
+ * with a Lorentzian broadening delta > 0:
+ *   A[j] = (1/pi) sum_a weight[a] delta / ((omega[j] - E[a])^2 + delta^2),
+ * E and weight as returned by mgw_qp_solve (weight_a = sum_p chi_pa^2).
+ *   E, weight [dim], omega [nomega] in; A [nomega] out; all device, FP64.
+ * Stream-ordered, no synchronisation.  Returns MGW_ERR_ARG for dim or nomega
+ * below 1, delta not positive or a null pointer.
+ */
+mgw_status mgw_spectral_function(mgw_handle* h, int dim, const double* E, const double* weight, double delta,
+                                 int nomega, const double* omega, double* A);
+
+/*
  * Warm-start network (not in the paper): three dense layers with SiLU,
  *   z1 = W1 x + b1, a1 = silu(z1); z2 = W2 a1 + b2, a2 = silu(z2); y = W3 a2 + b3.
  * params: FP32 master vector [W1 | b1 | W2 | b2 | W3 | b3] (W row-major

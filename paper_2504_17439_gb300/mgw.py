@@ -150,6 +150,10 @@ def load(path: str | None = None):
     lib.mgw_response_moments_batched.restype = _I
     lib.mgw_sync_status.argtypes = [_P]
     lib.mgw_sync_status.restype = _I
+    lib.mgw_naf_compress.argtypes = [_P, _I, _I, _I, _P, _D, _I, _P, _P, ctypes.POINTER(_I)]
+    lib.mgw_naf_compress.restype = _I
+    lib.mgw_spectral_function.argtypes = [_P, _I, _P, _P, _D, _I, _P, _P]
+    lib.mgw_spectral_function.restype = _I
     for name, args in _SIGS.items():
         fn = getattr(lib, name)
         fn.argtypes = [_P] + args
@@ -292,6 +296,26 @@ class Handle:
         self._check(self._lib.mgw_hf_core(self._h, nocc, nmo, naux, _ptr(eps, (nmo,), "eps"),
                                           _ptr(L, (naux, nmo, nmo), "L"), _ptr(hc)))
         return hc
+
+    def mgw_naf_compress(self, nocc, L, eps_naf=1e-5, all_pairs=False):
+        """Natural auxiliary functions (Sec. II D, Eq. 14).  Returns (L_naf
+        [n_naf][nmo][nmo], eigenvalues of M descending [naux])."""
+        naux, nmo = L.shape[0], L.shape[1]
+        out = torch.empty_like(L)
+        lam = torch.empty(naux, dtype=torch.float64, device=L.device)
+        k = _I(0)
+        self._check(self._lib.mgw_naf_compress(self._h, nocc, nmo - nocc, naux, _ptr(L, (naux, nmo, nmo), "L"),
+                                               float(eps_naf), int(bool(all_pairs)), _ptr(out), _ptr(lam),
+                                               ctypes.byref(k)))
+        return out[: k.value], lam
+
+    def mgw_spectral_function(self, E, weight, omega, delta):
+        """A(omega) of Eq. 12 from the poles (E, weight) of H~, broadening delta."""
+        dim, nw = E.shape[0], omega.shape[0]
+        A = torch.empty(nw, dtype=torch.float64, device=omega.device)
+        self._check(self._lib.mgw_spectral_function(self._h, dim, _ptr(E, (dim,), "E"), _ptr(weight, (dim,), "weight"),
+                                                    float(delta), nw, _ptr(omega, (nw,), "omega"), _ptr(A)))
+        return A
 
     # -- warm-start network -------------------------------------------------
     def _fptr(self, t, name):
