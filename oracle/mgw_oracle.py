@@ -41,6 +41,21 @@ garbled are listed in the docstrings that use them:
   R11 Spectral function (Eqs. 11-12): delta of Eq. 11 is a Lorentzian
       broadening, so A(w) = (1/pi) sum_a weight_a delta / ((w - E_a)^2 +
       delta^2) with weight_a = sum_p chi_pa^2.
+  Q1  qsGW (Sec. III D): Eq. 36 takes the real part, so the sign attached
+      to i delta in Eq. 37 does not enter V; Re Sigma_pq(w) =
+      sum_l v_pl v_ql (w - e_l) / ((w - e_l)^2 + delta^2).
+  Q2  Eq. 38 is printed without its sum over the decoupled poles l and
+      with Sigma_pq(eps_p) on the left; it is read as the static potential
+      itself, V_pq = sum_l (D_pl + D_ql) / (D_pl^2 + D_ql^2) v_pl v_ql
+      (1 - exp(-(D_pl^2 + D_ql^2) s)), D_pl = eps_p - e_l (Eq. 39), already
+      symmetric (the pair with D_pl = D_ql = 0 contributes its limit, 0).
+  Q3  Eq. 35: f[C] = h + J[rho] - K[rho]/2 with rho = 2 C_occ C_occ^T over
+      the nocc lowest orbitals; V is built in the orbitals C of the GW step,
+      carried to the reference basis as C V C^T and held fixed while the
+      field is solved (Pulay DIIS on the commutator F rho - rho F); the
+      outer loop rebuilds the moments from the new (eps, C) until the
+      orbital energies change by less than the tolerance.  The qsGW energies
+      are the eigenvalues of Eq. 35 (the mean-field Green's function).
 """
 from __future__ import annotations
 
@@ -646,6 +661,103 @@ def fsgw(h, L, eps, nocc, nmom_max, screening="tda", nq=48, max_outer=30, conv_e
         if dsig < conv_mom and dqp < conv_e:
             return dict(eps_qp=qp["eps_qp"], F=F, zeta=zeta, converged=True, history=history, mu=qp["mu"])
     return dict(eps_qp=qp["eps_qp"], F=F, zeta=zeta, converged=False, history=history, mu=qp["mu"])
+
+
+# ----------------------------------------------------------------------------
+# Quasiparticle self-consistent GW (Sec. III D, Eqs. 35-39)
+
+
+def decoupled_poles(chain):
+    """The external block of one chain, T = blocktridiag(alpha, beta), in its
+    eigenbasis (Sec. III D): T = U diag(e) U^T, couplings v = [coup, 0, ..] U,
+    so that this chain's part of Eq. 10 is sum_l v_pl v_ql / (w - e_l)."""
+    coup, alpha, beta = chain[:3]
+    nb, r = alpha.shape[0], alpha.shape[1]
+    T = np.zeros((nb * r, nb * r))
+    for i in range(nb):
+        T[i * r : (i + 1) * r, i * r : (i + 1) * r] = alpha[i]
+        if i + 1 < nb:
+            T[(i + 1) * r : (i + 2) * r, i * r : (i + 1) * r] = beta[i]
+            T[i * r : (i + 1) * r, (i + 1) * r : (i + 2) * r] = beta[i].T
+    e, U = np.linalg.eigh(T)
+    return coup @ U[:r, :], e
+
+
+def qsgw_potential(eps, hole, part, reg="srg", delta=1e-3, srg_s=100.0):
+    """Static potential of qsGW in the orbitals the chains were built in.
+    reg = "eta": Eq. 36 with the Lorentzian-regularised poles of Eq. 37
+    (reading Q1); reg = "srg": Eqs. 38-39 (reading Q2)."""
+    vh, eh = decoupled_poles(hole)
+    vp, ep = decoupled_poles(part)
+    v = np.concatenate([vh, vp], axis=1)
+    e = np.concatenate([eh, ep])
+    Dl = eps[:, None] - e[None, :]  # D_pl of Eq. 39
+    n = eps.size
+    V = np.zeros((n, n))
+    if reg == "eta":
+        R = Dl / (Dl * Dl + delta * delta)  # Re of one Eq. 37 denominator
+        A = np.einsum("pl,pl,ql->pq", R, v, v)  # A_pq = Re Sigma_pq(eps_p)
+        return 0.5 * (A + A.T)
+    if reg != "srg":
+        raise ValueError(f"unknown regularisation {reg!r}")
+    for l in range(e.size):
+        d = Dl[:, l]
+        s2 = d[:, None] ** 2 + d[None, :] ** 2
+        with np.errstate(invalid="ignore", divide="ignore"):
+            f = np.where(s2 > 0.0, (d[:, None] + d[None, :]) / s2 * (1.0 - np.exp(-s2 * srg_s)), 0.0)
+        V += f * np.outer(v[:, l], v[:, l])
+    return V
+
+
+def qsgw_scf(h, L, Vref, C, nocc, diis_space=8, max_iter=200, tol=1e-10):
+    """Eq. 35 with the static potential fixed (reading Q3): F = f[rho] + V,
+    rho from the nocc lowest eigenvectors, Pulay DIIS on F rho - rho F."""
+    rho = 2.0 * C[:, :nocc] @ C[:, :nocc].T
+    Fs, errs = [], []
+    for it in range(max_iter):
+        F = fock_build(h, L, rho) + Vref
+        err = F @ rho - rho @ F
+        Fs.append(F)
+        errs.append(err)
+        Fs, errs = Fs[-diis_space:], errs[-diis_space:]
+        Fx = diis_extrapolate(Fs, errs) if len(Fs) > 2 else F
+        e, C = np.linalg.eigh(Fx)
+        rho_new = 2.0 * C[:, :nocc] @ C[:, :nocc].T
+        drho = np.abs(rho_new - rho).max()
+        rho = rho_new
+        if drho < tol and np.abs(err).max() < 1e3 * tol:
+            break
+    F = fock_build(h, L, rho) + Vref
+    e, C = np.linalg.eigh(F)
+    return e, C, F, it + 1
+
+
+def qsgw(h, L, eps, nocc, nmom_max, reg="srg", delta=1e-3, srg_s=100.0, screening="tda", nq=48,
+         max_outer=60, conv=1e-8, C0=None):
+    """Quasiparticle self-consistent GW (Sec. III D).  h, L in the reference
+    orbital basis; eps and C0 the reference energies and orbitals there
+    (default C0 = 1: the basis is the canonical HF one, F[rho_HF] =
+    diag(eps)).  Each outer step builds the GW moments in the current
+    orbitals (eps^G = eps^W = eps, L rotated to C), their block-Lanczos
+    chains, the static potential (Eqs. 36-39) and then solves Eq. 35 with it
+    held fixed."""
+    e = eps.astype(float).copy()
+    C = np.eye(eps.size) if C0 is None else np.array(C0, dtype=float)
+    nmom, nblk = 2 * nmom_max + 2, nmom_max + 1
+    history = []
+    for outer in range(max_outer):
+        Lm = rotate_df(L, C)
+        W = response_moments(particle_hole_block(Lm, nocc), energy_differences(e, nocc), nmom, screening, nq)
+        sh, sp = sigma_moments(e, nocc, Lm, W)
+        V = qsgw_potential(e, block_lanczos(sh, nblk), block_lanczos(sp, nblk), reg, delta, srg_s)
+        Vref = C @ V @ C.T
+        e_new, C, F, k = qsgw_scf(h, L, Vref, C, nocc)
+        de = np.abs(e_new - e).max()
+        e = e_new
+        history.append(dict(outer=outer, de=de, scf_iter=k))
+        if de < conv:
+            return dict(eps=e, C=C, F=F, V=Vref, converged=True, history=history)
+    return dict(eps=e, C=C, F=F, V=Vref, converged=False, history=history)
 
 
 def hf_core_hamiltonian(eps, L, nocc):

@@ -109,6 +109,38 @@ def naf_pin_error(mod):
     return max(err, max(rel(b["sigma_hole"][n], a["sigma_hole"][n]) for n in range(6)))
 
 
+def qsgw_pin_error(mod):
+    # decoupled poles against Eq. 10's downfolding, both potentials against
+    # their expansions in the first two moments, the Hartree-Fock state of the
+    # field without a potential, and the fixed point of Eq. 35
+    eps, L = system(scale=3.0)
+    r = orc.g0w0(eps, L, 3, 2)
+    hole, part = r["hole"][:3], r["part"][:3]
+    nmo = eps.size
+    H = orc.upfolded_hamiltonian(np.zeros((nmo, nmo)), hole, part)
+    Wt, dt = H[:nmo, nmo:], H[nmo:, nmo:]
+    (vh, eh), (vp, ep) = mod.decoupled_poles(hole), mod.decoupled_poles(part)
+    v, e = np.concatenate([vh, vp], axis=1), np.concatenate([eh, ep])
+    z = 0.3 + 0.05j
+    err = rel((v / (z - e)) @ v.T, Wt @ np.linalg.solve(z * np.eye(dt.shape[0]) - dt, Wt.T))
+    M0 = r["sigma_hole"][0] + r["sigma_part"][0]
+    M1 = r["sigma_hole"][1] + r["sigma_part"][1]
+    E = np.diag(eps)
+    err = max(err, rel(mod.qsgw_potential(eps, hole, part, "srg", srg_s=1e-9), 1e-9 * (E @ M0 + M0 @ E - 2.0 * M1)))
+    err = max(err, rel(mod.qsgw_potential(eps, hole, part, "eta", delta=1e5), (0.5 * (E @ M0 + M0 @ E) - M1) / 1e10))
+    h = orc.hf_core_hamiltonian(eps, L, 3)
+    e0 = mod.qsgw_scf(h, L, np.zeros((nmo, nmo)), np.eye(nmo), 3)[0]
+    err = max(err, np.abs(e0 - eps).max())
+    q = mod.qsgw(h, L, eps, 3, 2, conv=1e-10)
+    e, C = q["eps"], q["C"]
+    Lm = orc.rotate_df(L, C)
+    W = orc.response_moments(orc.particle_hole_block(Lm, 3), orc.energy_differences(e, 3), 6)
+    sh, sp = orc.sigma_moments(e, 3, Lm, W)
+    V = orc.qsgw_potential(e, orc.block_lanczos(sh, 3), orc.block_lanczos(sp, 3))
+    F = orc.fock_build(h, L, 2.0 * C[:, :3] @ C[:, :3].T) + C @ V @ C.T
+    return max(err, np.abs(F @ C - C * e[None, :]).max() * 1e2)
+
+
 CASES = [
     # (functions, old, new, pin, screening)
     (["tda_response_moments"], "T * D[None, :] + 2.0 *", "T * D[None, :] + 1.0 *", "sigma", "tda"),
@@ -140,6 +172,13 @@ CASES = [
     (["naf_basis"], "return U[:, lam > eps_naf], lam", "return U[:, lam >= -1.0], lam", "naf", None),
     (["naf_basis"], "lam, U = lam[::-1], U[:, ::-1]", "lam, U = lam[::-1], U", "naf", None),
     (["naf_compress"], "np.tensordot(U.T, L, axes=1)", "np.tensordot(U.T, L, axes=1) * 1.01", "naf", None),
+    (["qsgw_potential"], "R = Dl / (Dl * Dl + delta * delta)", "R = Dl / (Dl * Dl + 2.0 * delta * delta)", "qsgw", None),
+    (["qsgw_potential"], "return 0.5 * (A + A.T)", "return A", "qsgw", None),
+    (["qsgw_potential"], "(1.0 - np.exp(-s2 * srg_s))", "(1.0 - np.exp(-s2 * srg_s * 0.5))", "qsgw", None),
+    (["qsgw_potential"], "(d[:, None] + d[None, :]) / s2", "(d[:, None] - d[None, :]) / s2", "qsgw", None),
+    (["decoupled_poles"], "return coup @ U[:r, :], e", "return coup @ U[:r, :], -e", "qsgw", None),
+    (["qsgw_scf"], "rho_new = 2.0 * C[:, :nocc]", "rho_new = 1.0 * C[:, :nocc]", "qsgw", None),
+    (["qsgw"], "Vref = C @ V @ C.T", "Vref = C.T @ V @ C", "qsgw", None),
 ]
 
 
@@ -155,6 +194,8 @@ def test_pins_catch_planted_mistake(case):
         err = spectral_pin_error(mod)
     elif pin == "naf":
         err = naf_pin_error(mod)
+    elif pin == "qsgw":
+        err = qsgw_pin_error(mod)
     else:
         err = qp_pin_error(mod)
     assert not (err < 1e-6), f"planted mistake went unnoticed: {old!r} -> {new!r} (err {err})"
@@ -168,4 +209,5 @@ def test_unmutated_copy_passes_every_pin():
     assert qp_pin_error(mod) < 1e-9
     assert spectral_pin_error(mod) < 1e-10
     assert naf_pin_error(mod) < 1e-10
+    assert qsgw_pin_error(mod) < 1e-6
     assert math.isfinite(lanczos_pin_error(orc))
