@@ -49,6 +49,16 @@ garbled are listed in the docstrings that use them:
       itself, V_pq = sum_l (D_pl + D_ql) / (D_pl^2 + D_ql^2) v_pl v_ql
       (1 - exp(-(D_pl^2 + D_ql^2) s)), D_pl = eps_p - e_l (Eq. 39), already
       symmetric (the pair with D_pl = D_ql = 0 contributes its limit, 0).
+  S1  scGW, Algorithm 5: the physical block of H~ stays the reference
+      orbitals (f + Sigma_inf = diag(eps), R8), so the map to the
+      quasi-molecular orbitals (QMOs) is the physical rows chi_px of the
+      current H~'s eigenvectors; the printed accumulation chi^ <- chi^ chi is
+      read as chi^ = chi (one factor, not a running product).
+  S2  The occupied QMOs are the Aufbau-occupied poles of Eq. 40 (reading
+      R7): the m lowest; they are the holes of Eqs. 6-7 and the i of the
+      (i, a) space, the rest the particles and the a.
+  S3  scGW stops when the QP energies of Eq. 34 change by less than the
+      tolerance between iterations.
   Q3  Eq. 35: f[C] = h + J[rho] - K[rho]/2 with rho = 2 C_occ C_occ^T over
       the nocc lowest orbitals; V is built in the orbitals C of the GW step,
       carried to the reference basis as C V C^T and held fixed while the
@@ -192,10 +202,13 @@ def sigma_moments(eps: np.ndarray, nocc: int, L: np.ndarray, W: np.ndarray, rows
     (all x at once, one matrix product per x), then
       Sigma(n,<)_pq = 2 sum_t C(n,t) (-1)^t sum_k eps_k^(n-t) W^(t)_{pk,qk}
       Sigma(n,>)_pq = 2 sum_t C(n,t)        sum_c eps_c^(n-t) W^(t)_{pc,qc}.
-    `rows` restricts p to a subset (the full q range is returned).
+    `rows` restricts p to a subset (the full q range is returned).  The
+    Green's-function index x may run over a larger space than p, q (the
+    quasi-molecular orbitals of scGW, Algorithm 5): L is then V^_{Q,qx}
+    [naux][nmo][nx] and eps holds the nx energies eps_x, holes first.
     """
     nmom = W.shape[0]
-    nmo = eps.size
+    nmo, nx = L.shape[1], eps.size
     p_idx = np.arange(nmo) if rows is None else np.asarray(rows)
     Lx = np.ascontiguousarray(L.transpose(2, 0, 1))  # [x][Q][q] = V_{Q,qx}
     Lxp = np.ascontiguousarray(Lx[:, :, p_idx].transpose(0, 2, 1))  # [x][p][P] = V_{P,px}
@@ -203,7 +216,7 @@ def sigma_moments(eps: np.ndarray, nocc: int, L: np.ndarray, W: np.ndarray, rows
     sp = np.zeros((nmom, p_idx.size, nmo))
     for t in range(nmom):
         Wx = (Lxp @ W[t]) @ Lx  # [x][p][q] = W^(t)_{px,qx}
-        for hole, xs, out in ((True, slice(0, nocc), sh), (False, slice(nocc, nmo), sp)):
+        for hole, xs, out in ((True, slice(0, nocc), sh), (False, slice(nocc, nx), sp)):
             sign = -1.0 if hole else 1.0
             for n in range(t, nmom):
                 wgt = 2.0 * math.comb(n, t) * sign**t * eps[xs] ** (n - t)
@@ -661,6 +674,50 @@ def fsgw(h, L, eps, nocc, nmom_max, screening="tda", nq=48, max_outer=30, conv_e
         if dsig < conv_mom and dqp < conv_e:
             return dict(eps_qp=qp["eps_qp"], F=F, zeta=zeta, converged=True, history=history, mu=qp["mu"])
     return dict(eps_qp=qp["eps_qp"], F=F, zeta=zeta, converged=False, history=history, mu=qp["mu"])
+
+
+# ----------------------------------------------------------------------------
+# Fully self-consistent GW on quasi-molecular orbitals (Sec. III E, Algorithm 5)
+
+
+def qmo_tensors(L, chi, m):
+    """The DF tensor distributed over the QMOs of H~ (Algorithm 5, reading
+    S1): V^_{Q,px} = sum_q L_{Q,pq} chi_qx for every pole x, and
+    V_{Q,ia} = sum_pq chi_pi L_{Q,pq} chi_qa over occupied i < m <= a (S2)."""
+    Vhat = np.einsum("Qpq,qx->Qpx", L, chi, optimize=True)
+    Via = np.einsum("pi,Qpx->Qix", chi[:, :m], Vhat[:, :, m:], optimize=True)
+    return Vhat, Via.reshape(L.shape[0], -1)
+
+
+def scgw(eps, L, nocc, nmom_max, screening="tda", nq=48, g0=False, w0=False, conv=1e-6, max_iter=40):
+    """scGW, GW0 (w0) or G0W (g0) of Algorithm 5 with f + Sigma_inf =
+    diag(eps) (R8).  Each iteration builds the response moments over the
+    current (i, a) space, the self-energy moments over the current x space,
+    the chains and H~, then (unless g0) moves G's space to the QMOs of H~
+    with eps^G = E and (unless w0) the (i, a) space to occupied x virtual
+    QMOs with eps^W = E (readings S1-S3)."""
+    nelec = 2.0 * nocc
+    f = np.diag(eps)
+    nmom, nblk = 2 * nmom_max + 2, nmom_max + 1
+    epsG, epsW, mG, mW = eps.copy(), eps.copy(), nocc, nocc
+    Vhat, Via = L, particle_hole_block(L, nocc)
+    prev = None
+    history = []
+    for it in range(max_iter):
+        W = response_moments(Via, energy_differences(epsW, mW), nmom, screening, nq)
+        sh, sp = sigma_moments(epsG, mG, Vhat, W)
+        qp = qp_solve(f, block_lanczos(sh, nblk)[:3], block_lanczos(sp, nblk)[:3], nelec)
+        d = np.abs(qp["eps_qp"] - prev).max() if prev is not None else np.inf
+        history.append(dict(iteration=it, dqp=d, poles=qp["E"].size, nelec=qp["nelec"]))
+        prev = qp["eps_qp"]
+        if d < conv:
+            return dict(qp, converged=True, history=history)
+        Vq, Vq_ia = qmo_tensors(L, qp["chi"], qp["m"])
+        if not g0:
+            epsG, mG, Vhat = qp["E"], qp["m"], Vq
+        if not w0:
+            epsW, mW, Via = qp["E"], qp["m"], Vq_ia
+    return dict(qp, converged=False, history=history)
 
 
 # ----------------------------------------------------------------------------

@@ -187,3 +187,46 @@ def naf_metric_pairs(L, nocc, pairs):
             col = L[:, v, w]
             M += np.outer(col, col)
     return M
+
+
+def sigma_lehmann_general(Ex, mx, Vhat, Via, D, nmom):
+    """TDA self-energy moments for a Green's function with poles E_x (holes
+    x < mx) and couplings V^_{Q,px}, screened over an (i, a) space with
+    energy differences D and V_{Q,ia}: explicit A = D + 2 V^T V, its
+    eigenpairs, residues w_{p x nu} = sqrt(2) sum_ia (px|ia) X_{ia,nu}, and
+    the Lehmann sums (E_x -+ Omega_nu)^n."""
+    Om, X = np.linalg.eigh(np.diag(D) + 2.0 * Via.T @ Via)
+    w = np.sqrt(2.0) * np.einsum("Ppx,Pj,jn->pxn", Vhat, Via, X, optimize=True)
+    nmo = Vhat.shape[1]
+    sh = np.zeros((nmom, nmo, nmo))
+    sp = np.zeros((nmom, nmo, nmo))
+    for n in range(nmom):
+        eh = (Ex[:mx, None] - Om[None, :]) ** n
+        ep = (Ex[mx:, None] + Om[None, :]) ** n
+        sh[n] = np.einsum("pkn,qkn,kn->pq", w[:, :mx], w[:, :mx], eh)
+        sp[n] = np.einsum("pcn,qcn,cn->pq", w[:, mx:], w[:, mx:], ep)
+    return sh, sp
+
+
+def scgw_lehmann(orc, eps, L, nocc, nmom_max, g0, w0, iterations):
+    """Algorithm 5 with every self-energy moment taken from the explicit
+    Lehmann convolution (sigma_lehmann_general); the chains, H~ and the
+    Aufbau filling come from the oracle module passed in.  Returns the QP
+    energies of each iteration."""
+    nmom, nblk, f = 2 * nmom_max + 2, nmom_max + 1, np.diag(eps)
+    EG, EW, mG, mW = eps, eps, nocc, nocc
+    Vhat, Via = L, L[:, :nocc, nocc:].reshape(L.shape[0], -1)
+    out = []
+    for _ in range(iterations):
+        D = (EW[None, mW:] - EW[:mW, None]).ravel()
+        sh, sp = sigma_lehmann_general(EG, mG, Vhat, Via, D, nmom)
+        qp = orc.qp_solve(f, orc.block_lanczos(sh, nblk)[:3], orc.block_lanczos(sp, nblk)[:3], 2.0 * nocc)
+        out.append(qp["eps_qp"])
+        chi, m = qp["chi"], qp["m"]
+        V2 = np.einsum("Ppq,qx->Ppx", L, chi)
+        if not g0:
+            EG, mG, Vhat = qp["E"], m, V2
+        if not w0:
+            EW, mW = qp["E"], m
+            Via = np.einsum("pi,Ppa->Pia", chi[:, :m], V2[:, :, m:]).reshape(L.shape[0], -1)
+    return out

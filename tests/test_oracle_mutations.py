@@ -141,6 +141,23 @@ def qsgw_pin_error(mod):
     return max(err, np.abs(F @ C - C * e[None, :]).max() * 1e2)
 
 
+def scgw_pin_error(mod):
+    # the self-energy moments over a QMO space against the Lehmann
+    # convolution, and three scGW iterations against the Lehmann driver
+    eps, L = system(scale=3.0)
+    g = orc.g0w0(eps, L, 3, 2)
+    E, m = g["E"], g["m"]
+    Vhat, Via = mod.qmo_tensors(L, g["chi"], m)
+    D = orc.energy_differences(E, m)
+    sh, sp = mod.sigma_moments(E, m, Vhat, orc.response_moments(Via, D, 6))
+    Vh0, Via0 = orc.qmo_tensors(L, g["chi"], m)
+    bh, bp = brute.sigma_lehmann_general(E, m, Vh0, Via0, D, 6)
+    err = max(max(rel(sh[n], bh[n]), rel(sp[n], bp[n])) for n in range(6))
+    ref = brute.scgw_lehmann(orc, eps, L, 3, 1, False, False, 3)
+    got = mod.scgw(eps, L, 3, 1, max_iter=3, conv=0.0)["eps_qp"]
+    return max(err, np.abs(got - ref[2]).max() * 1e3)
+
+
 CASES = [
     # (functions, old, new, pin, screening)
     (["tda_response_moments"], "T * D[None, :] + 2.0 *", "T * D[None, :] + 1.0 *", "sigma", "tda"),
@@ -179,6 +196,10 @@ CASES = [
     (["decoupled_poles"], "return coup @ U[:r, :], e", "return coup @ U[:r, :], -e", "qsgw", None),
     (["qsgw_scf"], "rho_new = 2.0 * C[:, :nocc]", "rho_new = 1.0 * C[:, :nocc]", "qsgw", None),
     (["qsgw"], "Vref = C @ V @ C.T", "Vref = C.T @ V @ C", "qsgw", None),
+    (["scgw"], 'epsG, mG, Vhat = qp["E"], qp["m"], Vq', 'epsG, mG, Vhat = qp["E"], nocc, Vq', "scgw", None),
+    (["qmo_tensors"], 'np.einsum("Qpq,qx->Qpx", L, chi,', 'np.einsum("Qpq,qx->Qpx", L, chi / np.sqrt((chi**2).sum(0)),', "scgw", None),
+    (["qmo_tensors"], 'np.einsum("pi,Qpx->Qix", chi[:, :m],', 'np.einsum("pi,Qpx->Qix", chi[:, :m][:, ::-1],', "scgw", None),
+    (["sigma_moments"], "(False, slice(nocc, nx), sp)", "(False, slice(nocc, nmo), sp)", "scgw", None),
 ]
 
 
@@ -196,6 +217,8 @@ def test_pins_catch_planted_mistake(case):
         err = naf_pin_error(mod)
     elif pin == "qsgw":
         err = qsgw_pin_error(mod)
+    elif pin == "scgw":
+        err = scgw_pin_error(mod)
     else:
         err = qp_pin_error(mod)
     assert not (err < 1e-6), f"planted mistake went unnoticed: {old!r} -> {new!r} (err {err})"
@@ -210,4 +233,5 @@ def test_unmutated_copy_passes_every_pin():
     assert spectral_pin_error(mod) < 1e-10
     assert naf_pin_error(mod) < 1e-10
     assert qsgw_pin_error(mod) < 1e-6
+    assert scgw_pin_error(mod) < 1e-6
     assert math.isfinite(lanczos_pin_error(orc))
