@@ -144,26 +144,33 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        rows = []
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) >= 8:
-                rows.append(parts)
+        with open(self.path) as f:
+            lines = f.readlines()
         os.unlink(self.path)
-        if not rows:
-            return None
+        return summarise_clocks(lines)
 
-        def num(x):
-            try:
-                return float(x)
-            except ValueError:
-                return float("nan")
-        sm = [num(r[0]) for r in rows]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower() == "active"})
-        loaded = [s for s in sm if s == s]
-        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": num(rows[0][1]),
-                "power_w_max": max(num(r[2]) for r in rows), "samples": len(rows), "reasons": reasons}
+
+def summarise_clocks(lines):
+    """nvidia-smi samples (ClockSampler.FIELDS, csv, no header, no units) ->
+    median SM clock, its maximum, peak power, sample count and every throttle
+    reason seen active; None without a well-formed sample."""
+    rows = [[p.strip() for p in line.split(",")] for line in lines]
+    rows = [r for r in rows if len(r) >= 8]
+    if not rows:
+        return None
+
+    def num(x):
+        try:
+            return float(x)
+        except ValueError:
+            return float("nan")
+    sm = [num(r[0]) for r in rows]
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower() == "active"})
+    loaded = [v for v in sm if v == v]
+    power = [v for v in (num(r[2]) for r in rows) if v == v]
+    return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": num(rows[0][1]),
+            "power_w_max": max(power) if power else None, "samples": len(rows), "reasons": reasons}
 
 
 # ---------------------------------------------------------------------------- CPU oracle

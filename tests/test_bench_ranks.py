@@ -76,3 +76,21 @@ def test_traffic_hash_ignores_comments_but_not_code():
     src = "int f(int x) {  // doubles x\n  /* a\n block */ return 2 * x;\n}\n"
     assert bench.code_of(src) == bench.code_of("int f(int x) {\n\n   return 2 * x;\n}")
     assert bench.code_of(src) != bench.code_of(src.replace("2 * x", "3 * x"))
+
+
+def test_clock_samples_summarised_with_every_active_throttle_reason():
+    import bench
+
+    lines = [
+        "2070, 2070, 512.3, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n",
+        "1965, 2070, 1398.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active\n",
+        "[N/A], 2070, [N/A], 0x0, Not Active, Not Active, Not Active, Not Active\n",
+        "2070, 2070, 880.1, 0x0000000000000008, Active, Not Active, Not Active, Not Active\n",
+        "garbled line\n",
+    ]
+    c = bench.summarise_clocks(lines)
+    assert c["samples"] == 4
+    assert c["sm_mhz"] == 2070.0 and c["sm_max_mhz"] == 2070.0
+    assert c["power_w_max"] == 1398.0
+    assert c["reasons"] == ["hw_slowdown", "sw_power_cap"]
+    assert bench.summarise_clocks(["garbled\n"]) is None
