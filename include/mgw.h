@@ -396,6 +396,26 @@ mgw_status mgw_spectral_function(mgw_handle* h, int dim, const double* E, const 
                                  int nomega, const double* omega, double* A);
 
 /*
+ * mgw_qsgw_potential -- the static potential of qsGW (Sec. III D) from the
+ * hole and particle chains of mgw_block_lanczos (same padded layout: coup
+ * [nmo][nmo] with rank columns used, alpha [nblk][nmo][nmo], beta
+ * [nblk-1][nmo][nmo] with rank x rank blocks used).  Each chain's external
+ * block is diagonalised, T = U diag(e) U^T, giving couplings v = [coup, 0..] U
+ * and pole energies e (pole decoupling); with D_pl = eps_p - e_l:
+ *   reg 0 (Eqs. 36-37): V = (A + A^T)/2, A_pq = sum_l v_pl v_ql D_pl / (D_pl^2 + delta^2)
+ *   reg 1 (Eqs. 38-39): V_pq = sum_l (D_pl + D_ql) / (D_pl^2 + D_ql^2) v_pl v_ql (1 - exp(-(D_pl^2 + D_ql^2) s))
+ * The pair with D_pl = D_ql = 0 contributes 0.
+ *   eps [nmo] in (the energies the chains were built with); V [nmo][nmo] out;
+ *   all device, FP64.  The eigensolves (cuSOLVER syevd) synchronise the stream.
+ * Returns MGW_ERR_ARG for bad sizes, reg not 0 or 1, delta <= 0 (reg 0),
+ * s < 0 (reg 1) or missing blocks; MGW_ERR_NO_CONV if an eigensolve fails.
+ */
+mgw_status mgw_qsgw_potential(mgw_handle* h, int nmo, int nblk, int rank_h, int rank_p, const double* eps,
+                              const double* coup_h, const double* alpha_h, const double* beta_h,
+                              const double* coup_p, const double* alpha_p, const double* beta_p, int reg,
+                              double delta, double srg_s, double* V);
+
+/*
  * Warm-start network (not in the paper): three dense layers with SiLU,
  *   z1 = W1 x + b1, a1 = silu(z1); z2 = W2 a1 + b2, a2 = silu(z2); y = W3 a2 + b3.
  * params: FP32 master vector [W1 | b1 | W2 | b2 | W3 | b3] (W row-major

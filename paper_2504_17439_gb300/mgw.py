@@ -154,6 +154,8 @@ def load(path: str | None = None):
     lib.mgw_naf_compress.restype = _I
     lib.mgw_spectral_function.argtypes = [_P, _I, _P, _P, _D, _I, _P, _P]
     lib.mgw_spectral_function.restype = _I
+    lib.mgw_qsgw_potential.argtypes = [_P, _I, _I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _I, _D, _D, _P]
+    lib.mgw_qsgw_potential.restype = _I
     for name, args in _SIGS.items():
         fn = getattr(lib, name)
         fn.argtypes = [_P] + args
@@ -316,6 +318,17 @@ class Handle:
         self._check(self._lib.mgw_spectral_function(self._h, dim, _ptr(E, (dim,), "E"), _ptr(weight, (dim,), "weight"),
                                                     float(delta), nw, _ptr(omega, (nw,), "omega"), _ptr(A)))
         return A
+
+    def mgw_qsgw_potential(self, nmo, nblk, rank_h, rank_p, eps, hole, part, reg="srg", delta=1e-3, srg_s=100.0):
+        """Static qsGW potential (Sec. III D, Eqs. 36-39) from the chains
+        hole/part = (coup, alpha, beta) as returned by mgw_block_lanczos."""
+        V = torch.empty((nmo, nmo), dtype=torch.float64, device=eps.device)
+        ch, ah, bh = hole
+        cp, ap, bp = part
+        self._check(self._lib.mgw_qsgw_potential(self._h, nmo, nblk, rank_h, rank_p, _ptr(eps, (nmo,), "eps"),
+                                                 _ptr(ch), _ptr(ah), _ptr(bh), _ptr(cp), _ptr(ap), _ptr(bp),
+                                                 0 if reg == "eta" else 1, float(delta), float(srg_s), _ptr(V)))
+        return V
 
     # -- warm-start network -------------------------------------------------
     def _fptr(self, t, name):
