@@ -50,11 +50,22 @@ typedef enum {
 typedef enum { MGW_TDA = 0, MGW_RPA = 1 } mgw_screening;
 
 /* Arithmetic of the bulk contractions.  FP64: float64 FMA units throughout.
- * FP64_TC: the dominant contraction of the Sigma build on the BF16 tensor
- * cores as an FP64-accurate digit-sliced product (see mgw_gemm_fp64_emu).
+ * FP64_TC: the response and Sigma-build contractions on the BF16 tensor
+ * cores as FP64-accurate digit-sliced products (see mgw_gemm_fp64_emu), 28
+ * BF16 products per product.
+ * MIXED: the DF tensor enters as a BF16 hi/lo split on one fixed-point grid:
+ * L (and V for the TDA response) rounded to a multiple of 2^(e-16) where
+ * max |L| < 2^(e-1), i.e. to 16 bits of the largest element, and carried as
+ * two BF16 digits; the moment-carrying operands (eta~, W, Z) keep seven
+ * digits and every digit product is exact, 13 BF16 products per product.
+ * The results are the FP64-accurate moments of the system with the rounded
+ * tensor, a consistent moment sequence (no amplification by the block
+ * Lanczos step): QP energies move by a few 1e-5 to 1e-4 meV at the frontier
+ * and by at most about 0.06 meV elsewhere on the synthetic workloads (N = 5
+ * and 7).  The RPA response takes V unrounded (as FP64_TC).
  * BF16X3 is only the standalone mgw_gemm_bf16x3 product (FP32 accumulation
  * is too coarse for the moment-to-Lanczos step, so no path uses it). */
-typedef enum { MGW_FP64 = 0, MGW_BF16X3 = 1, MGW_FP64_TC = 2 } mgw_precision;
+typedef enum { MGW_FP64 = 0, MGW_BF16X3 = 1, MGW_FP64_TC = 2, MGW_MIXED = 3 } mgw_precision;
 
 typedef struct mgw_handle mgw_handle;
 
@@ -493,7 +504,8 @@ mgw_status mgw_gemm_bf16x3(mgw_handle* h, int M, int N, int K,
  *   cuda_stream: cudaStream_t (or NULL) on which the work is queued
  *   eps_W [nmo], Lov [naux][nocc*nvir] in; Wmom [nmom][naux][naux] out
  * Returns MGW_ERR_ARG on bad sizes or null pointers, MGW_ERR_CUDA if a launch
- * or the symbol lookup fails.
+ * or the symbol lookup fails.  There is no handle, so no mgw_last_error text:
+ * the status code is all a failing call reports.
  */
 mgw_status mgw_response_moments_tda_noalloc(void* cuda_stream, int nocc, int nvir, int naux, int nmom,
                                             const double* eps_W, const double* Lov, double* Wmom);

@@ -393,14 +393,14 @@ extern "C" mgw_status mgw_sigma_moments_batched(mgw_handle* h, const mgw_options
     if (sys[s].nocc < 1 || sys[s].nvir < 1 || sys[s].naux < 1 || !sys[s].eps || !sys[s].L || !sys[s].sig_hole ||
         !sys[s].sig_part)
       return fail(h, MGW_ERR_ARG, "mgw_sigma_moments_batched: bad system %d", s);
-  if (o->precision != MGW_FP64 && o->precision != MGW_FP64_TC)
+  if (o->precision != MGW_FP64 && o->precision != MGW_FP64_TC && o->precision != MGW_MIXED)
     return fail(h, MGW_ERR_UNSUPPORTED, "mgw_sigma_moments_batched: precision %d not built", o->precision);
   MGW_CUDA(h, cudaSetDevice(h->device));
   if (!h->batched_plan) {
     h->batched_plan = new BatchedPlan();
     h->batched_plan_free = free_plan;
   }
-  if (o->precision == MGW_FP64_TC)
+  if (o->precision == MGW_FP64_TC || o->precision == MGW_MIXED)
     return batched_tc(h, static_cast<BatchedPlan*>(h->batched_plan), o, nsys, nmom, sys);
   const int rounds = 4;  // Green's-function chunks per sector and system
 
@@ -463,7 +463,11 @@ extern "C" mgw_status mgw_sigma_moments_batched(mgw_handle* h, const mgw_options
   }
   if (plan->shape_key != shape_key) plan->tuned = false;
 
-  // tile shapes: time the candidates of the non-triangular stages on this table
+  // tile shapes: time the candidates of the non-triangular stages on this
+  // table.  The stages run here on whatever the workspace holds (their inputs
+  // are not recomputed first): FP64 FMA issue and memory traffic do not depend
+  // on the values, NaN and subnormal operands included, so the timing of a
+  // candidate is that of a real build of the same shapes.
   if (o->batch_autotune && !plan->tuned) {
     int best[kStKinds] = {0, 0, 0, 0};
     for (int kind : {kStT, kStY}) {

@@ -18,14 +18,19 @@
 // therefore come before any stream capture.
 #include "mgw_internal.h"
 
+#include <atomic>
+
 namespace mgw {
 
 // 4 Mi doubles = 32 MiB: D[ov] followed by T[naux][ov]
 constexpr long kNoallocScratchDoubles = 4L * 1024 * 1024;
 static __device__ __align__(256) double g_tda_scratch[kNoallocScratchDoubles];
 
+// device address of the array per device, published once looked up; two host
+// threads making their first call on one device at the same time both look it
+// up and store the same address
 constexpr int kMaxDevices = 64;
-static double* g_scratch_ptr[kMaxDevices] = {nullptr};
+static std::atomic<double*> g_scratch_ptr[kMaxDevices];
 
 }  // namespace mgw
 
@@ -39,16 +44,18 @@ extern "C" mgw_status mgw_response_moments_tda_noalloc(void* cuda_stream, int no
   if (ov + (long)naux * ov > kNoallocScratchDoubles) return MGW_ERR_UNSUPPORTED;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MGW_ERR_CUDA;
-  if (!g_scratch_ptr[dev]) {
+  double* D = g_scratch_ptr[dev].load(std::memory_order_acquire);
+  if (!D) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_tda_scratch) != cudaSuccess || !p) return MGW_ERR_CUDA;
-    g_scratch_ptr[dev] = static_cast<double*>(p);
+    D = static_cast<double*>(p);
+    g_scratch_ptr[dev].store(D, std::memory_order_release);
   }
-  double* D = g_scratch_ptr[dev];
   double* T = D + ((ov + 31) / 32) * 32;  // keep T 256-byte aligned
   if ((T - D) + (long)naux * ov > kNoallocScratchDoubles) return MGW_ERR_UNSUPPORTED;
 
-  // a handle on the stack: stream only, no solver, no workspace
+  // a handle on the stack: stream only, no solver, no workspace; its error
+  // text goes with it, so callers get the status code alone
   mgw_handle hs;
   mgw_handle* h = &hs;
   h->device = dev;

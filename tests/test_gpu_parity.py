@@ -54,10 +54,18 @@ def system(nocc, nvir, naux, seed, scale=1.0):
     return eps, L
 
 
+def precision_of(name):
+    from paper_2504_17439_gb300 import mgw
+
+    return {"fp64": mgw.MGW_FP64, "fp64_tc": mgw.MGW_FP64_TC, "mixed": mgw.MGW_MIXED}[name]
+
+
 @pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("screening,precision", [("tda", "fp64"), ("rpa", "fp64"), ("tda", "fp64_tc"),
-                                                ("rpa", "fp64_tc")])
+                                                ("rpa", "fp64_tc"), ("tda", "mixed"), ("rpa", "mixed")])
 def test_response_moments(h, shape, screening, precision):
+    """Under MGW_MIXED the TDA response is that of V on its 16-bit grid (the
+    oracle takes V rounded the same way) and the RPA that of V itself."""
     from paper_2504_17439_gb300 import mgw
 
     nocc, nvir, naux, N, seed = shape
@@ -65,9 +73,9 @@ def test_response_moments(h, shape, screening, precision):
     nmom = 2 * N + 2
     D = orc.energy_differences(eps, nocc)
     Lov = orc.particle_hole_block(L, nocc)
-    ref = orc.response_moments(Lov, D, nmom, screening, 48)
-    o = mgw.options(screening=mgw.MGW_TDA if screening == "tda" else mgw.MGW_RPA,
-                    precision=mgw.MGW_FP64 if precision == "fp64" else mgw.MGW_FP64_TC)
+    Vref = orc.fixed_point_grid(Lov) if (precision, screening) == ("mixed", "tda") else Lov
+    ref = orc.response_moments(Vref, D, nmom, screening, 48)
+    o = mgw.options(screening=mgw.MGW_TDA if screening == "tda" else mgw.MGW_RPA, precision=precision_of(precision))
     got = host(h.mgw_response_moments(o, nocc, nvir, naux, nmom, dev(eps), dev(Lov)))
     for n in range(nmom):
         assert rel(got[n], ref[n]) < TOL, (n, rel(got[n], ref[n]))
@@ -83,18 +91,19 @@ def test_extract_ov(h, shape):
 
 @pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("xchunk", [0, 3])
-@pytest.mark.parametrize("precision", ["fp64", "fp64_tc"])
+@pytest.mark.parametrize("precision", ["fp64", "fp64_tc", "mixed"])
 def test_sigma_moments(h, shape, xchunk, precision):
-    """Both arithmetic paths of the Sigma build: FP64 FMA units, and the Y stage
-    on the tensor cores as an FP64-accurate digit-sliced product."""
+    """Every arithmetic path of the Sigma build: FP64 FMA units, the Y stage
+    and GEMM2 on the tensor cores as FP64-accurate digit-sliced products, and
+    the mixed mode (L on its 16-bit grid, which the oracle takes too)."""
     from paper_2504_17439_gb300 import mgw
 
     nocc, nvir, naux, N, seed = shape
     eps, L = system(nocc, nvir, naux, seed, scale=2.0)
     nmom = 2 * N + 2
     W = orc.tda_response_moments(orc.particle_hole_block(L, nocc), orc.energy_differences(eps, nocc), nmom)
-    rh, rp = orc.sigma_moments(eps, nocc, L, W)
-    o = mgw.options(xchunk=xchunk, precision=mgw.MGW_FP64 if precision == "fp64" else mgw.MGW_FP64_TC)
+    rh, rp = orc.sigma_moments(eps, nocc, orc.fixed_point_grid(L) if precision == "mixed" else L, W)
+    o = mgw.options(xchunk=xchunk, precision=precision_of(precision))
     gh, gp = h.mgw_sigma_moments(o, nocc, nvir, naux, nmom, dev(eps), dev(L), dev(W))
     gh, gp = host(gh), host(gp)
     for n in range(nmom):
@@ -216,20 +225,41 @@ def test_qp_solve_on_oracle_blocks(h, shape):
     assert np.abs(host(got["rho"]) - ref["rho"]).max() < 1e-9
 
 
+def oracle_g0w0_mixed(eps, L, nocc, N, screening):
+    """The oracle chain on the tensors MGW_MIXED contracts: the TDA response
+    on V rounded to its grid (the RPA on V itself), Sigma on L rounded to
+    its grid."""
+    D = orc.energy_differences(eps, nocc)
+    V = orc.particle_hole_block(L, nocc)
+    W = orc.response_moments(orc.fixed_point_grid(V) if screening == "tda" else V, D, 2 * N + 2, screening, 48)
+    sh, sp = orc.sigma_moments(eps, nocc, orc.fixed_point_grid(L), W)
+    hole, part = orc.block_lanczos(sh, N + 1), orc.block_lanczos(sp, N + 1)
+    qp = orc.qp_solve(np.diag(eps), hole[:3], part[:3], 2.0 * nocc)
+    return dict(sigma_hole=sh, sigma_part=sp, hole=hole, part=part, **qp)
+
+
 @pytest.mark.parametrize("screening,precision", [("tda", "fp64"), ("rpa", "fp64"), ("tda", "fp64_tc"),
-                                                ("rpa", "fp64_tc")])
+                                                ("rpa", "fp64_tc"), ("tda", "mixed"), ("rpa", "mixed")])
 def test_g0w0_end_to_end(h, screening, precision):
     from paper_2504_17439_gb300 import driver, mgw
 
     shape, seed = mgw_inputs.workload("g0w0-nmo24-naux72")
     eps, L = mgw_inputs.system(shape, seed)
-    ref = orc.g0w0(eps, L, shape.nocc, shape.nmom_max, screening)
-    o = mgw.options(precision=mgw.MGW_FP64 if precision == "fp64" else mgw.MGW_FP64_TC)
+    if precision == "mixed":
+        ref = oracle_g0w0_mixed(eps, L, shape.nocc, shape.nmom_max, screening)
+        plain = orc.g0w0(eps, L, shape.nocc, shape.nmom_max, screening)
+    else:
+        ref = orc.g0w0(eps, L, shape.nocc, shape.nmom_max, screening)
+    o = mgw.options(precision=precision_of(precision))
     r = driver.g0w0(h, dev(eps), dev(L), shape.nocc, shape.nmom_max,
                     mgw.MGW_TDA if screening == "tda" else mgw.MGW_RPA, opts=o)
     for n in range(shape.nmom):
         assert rel(host(r["sigma_hole"])[n], ref["sigma_hole"][n]) < TOL
         assert rel(host(r["sigma_part"])[n], ref["sigma_part"][n]) < TOL
+    # QP energies are held to 1e-8 Ha absolute rather than 1e-9 relative: the
+    # moment-to-block step amplifies a relative moment perturbation by about
+    # 1e2 per block (lanczos_sensitivity: 1e-16 on Sigma moves alpha_5 by
+    # about 2e-7 relative at N = 5), which the QP poles inherit only weakly
     assert np.abs(host(r["eps_qp"]) - ref["eps_qp"]).max() < 1e-8
     # quasiparticle poles (above) are well conditioned; the other poles inherit
     # the block-Lanczos conditioning (see lanczos_sensitivity): all are held to
@@ -241,6 +271,9 @@ def test_g0w0_end_to_end(h, screening, precision):
     assert np.abs(E[strong] - ref["E"][strong]).max() < 1e-7
     assert np.abs(w[strong] - ref["weight"][strong]).max() < 1e-5
     assert abs(r["mu"] - ref["mu"]) < 1e-8
+    if precision == "mixed":
+        # the mixed path's bar against the unrounded FP64 oracle: 1 meV
+        assert np.abs(host(r["eps_qp"]) - plain["eps_qp"]).max() < 3.6749e-5
 
 
 def test_evgw_matches_oracle(h):

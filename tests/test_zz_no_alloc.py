@@ -40,7 +40,7 @@ def test_noalloc_tda_matches_regular_entry_point_twice():
         nmom = 2 * N + 2
         Lov = torch.from_numpy(np.ascontiguousarray(L[:, :nocc, nocc:]).reshape(naux, -1)).cuda()
         e = torch.from_numpy(eps).cuda()
-        ref = h.mgw_response_moments(mgw.options(), nocc, nvir, naux, nmom, e, Lov).cpu().numpy()
+        ref = h.mgw_response_moments(mgw.options(screening=mgw.MGW_TDA), nocc, nvir, naux, nmom, e, Lov).cpu().numpy()
         for call in range(2):
             W = torch.full((nmom, naux, naux), float("nan"), dtype=torch.float64, device="cuda")
             st = fn(ctypes.c_void_p(stream.cuda_stream), nocc, nvir, naux, nmom, ctypes.c_void_p(e.data_ptr()),
