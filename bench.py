@@ -1,25 +1,30 @@
 #!/usr/bin/env python
 """Benchmark of the moment-conserving GW self-energy moment build on GB300.
 
-A step is one pass of the hot path over one synthetic molecule-sized system
-(nocc 60, nvir 340, naux 1600, nmom_max 7, TDA): particle-hole block,
-response moments W(t), hole/particle Sigma(n) moments, block Lanczos of both
-sectors, and the upfolded-Hamiltonian QP solve.  By default the bulk
-contractions run as FP64-accurate digit-sliced products on the BF16 tensor
-cores (--precision fp64_tc); --precision fp64 runs them on the FP64 units.
-With the tensor-core path the same run also times the plain FP64 path once
-and reports its Sigma-build time, the speedup and the largest QP-energy
-difference between the two (fp64_path).
+A step is one Sigma-moment build of one synthetic pigment-molecule-sized
+system (nocc 240, nvir 960, naux 4800, nmom_max 7, TDA; L is 55 GB in FP64):
+particle-hole block, response moments W(t) and hole/particle Sigma(n)
+moments, inputs resident in HBM.  Block Lanczos of both sectors and the
+upfolded-Hamiltonian QP solve run once after the timed region
+(post_sigma_s).  By default the bulk contractions run in the mixed mode
+(--precision mixed: the DF tensor as a BF16 hi/lo split on one fixed-point
+grid, every digit product exact, 13 BF16 products per product); fp64_tc is
+the FP64-accurate digit-sliced path (28 products) and fp64 the FP64 units.
+The mixed run also times the fp64_tc path once (build time, largest
+QP-energy difference) and estimates the FP64-unit build from that path's
+measured rate on the 400-orbital workload (compare).
 
-Metric: seconds per Sigma-moment build (response + Sigma moments, inputs
-resident in HBM), lower is better.  The JSON line also carries the full step
-time, an end-to-end number through the C ABI with host buffers (H2D of eps
+Metric: seconds per Sigma-moment build, lower is better.  The JSON line also
+carries an end-to-end number through the C ABI with host buffers (H2D of eps
 and L, D2H of both Sigma tensors inside the timed region), the roofline of
-the dominant kernel measured live with CUDA events, the CPU oracle timed on
-a bounded sample of the same workload, and SM clocks sampled during the run.
+the dominant kernel on the method's own flops measured live with CUDA events,
+the CPU oracle timed on a bounded sample of the same workload (every core and
+one thread, in child processes; extrapolated to one build), and SM clocks
+sampled during the run.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mgw|reference]
-                  [--precision fp64_tc|fp64] [--batched N]
+                  [--workload NAME] [--precision mixed|fp64_tc|fp64]
+                  [--batched N] [--fsgw N] [--extras]
 
 Multi-GPU (torchrun): every rank runs an independent replica of the whole
 step (the path is not sharded here); value = max-over-ranks timed seconds /
@@ -46,10 +51,9 @@ import numpy as np  # noqa: E402
 
 import mgw_inputs  # noqa: E402
 
-WORKLOAD = "g0w0-nmo400-naux1600"
+WORKLOAD = "g0w0-nmo1200-naux4800"
 METRIC = "sigma_moment_build_s"
 FP64_PEAK_GFLOPS = 1250.0  # nominal GB300 FP64 (DFMA) rate; the ALU bound of the FP64 path
-DIGIT_PRODUCTS = 28        # BF16 digit products per FP64-accurate tensor-core product (7 digits, levels <= 8)
 
 # DRAM bytes per launch of the dominant kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum averaged over the 32 launches of one step), from one
@@ -176,62 +180,142 @@ def summarise_clocks(lines):
 # ---------------------------------------------------------------------------- CPU oracle
 
 
-def oracle_sample(shape, eps, L, resp_rows=160, sig_rows=(4, 12)):
-    """Time the CPU oracle on a bounded sample of the workload and scale it to
-    one full Sigma-moment build: the TDA response for `resp_rows` of naux aux
-    rows (rows are independent, cost linear in rows), and Sigma moments for
-    two small sets of orbital rows p (a + b * rows fit, evaluated at nmo)."""
+def sample_inputs(shape, seed, xchunk):
+    """What the oracle sample needs of the workload's DF tensor: the
+    particle-hole block V [naux][ov] and the slab columns of the first
+    `xchunk` orbitals, L[:, :, :xchunk], drawn slab by slab (never the whole
+    tensor at once)."""
+    nocc, nmo, naux = shape.nocc, shape.nmo, shape.naux
+    eps = mgw_inputs.orbital_energies(shape.nocc, shape.nvir, seed)
+    Lov = np.empty((naux, nocc * shape.nvir))
+    Lx = np.empty((naux, nmo, xchunk))
+
+    def fill(q):
+        slab = mgw_inputs.df_slab(q, naux, nmo, seed)
+        Lov[q] = slab[:nocc, nocc:].ravel()
+        Lx[q] = slab[:, :xchunk]
+    import concurrent.futures
+    with concurrent.futures.ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+        list(ex.map(fill, range(naux)))
+    return eps, Lov, Lx
+
+
+def sample_plan(shape, threads):
+    """Aux rows of the response and Green's-function orbitals x of the Sigma
+    build (all orbital rows p) that one sample computes: about 1.5e12 flops
+    of each on every core, 2e11 on one thread.  Each part is a whole-width
+    slice of the build (full GEMM widths, so the oracle runs at its full-size
+    rate) and its cost is linear in the rows or orbitals taken."""
+    target = 1.5e12 if threads > 1 else 2e11
+    per_row = 4.0 * shape.nmom * shape.naux * shape.ov
+    per_x = 2.0 * shape.nmom * (shape.nmo * shape.naux ** 2 + shape.naux * shape.nmo ** 2)
+    resp_rows = int(min(shape.naux, max(min(4, shape.naux), math.ceil(target / per_row))))
+    sig_x = int(min(shape.nmo, max(1, math.ceil(target / per_x))))
+    return resp_rows, sig_x
+
+
+def oracle_sample(shape, eps, Lov, Lx, resp_rows):
+    """Time the CPU oracle on a bounded sample of one Sigma-moment build and
+    scale it to the whole build: the TDA response for `resp_rows` aux rows
+    (each row of eta~(n) = V A^n is independent) and the Sigma moments of
+    every orbital row over the Green's-function orbitals x that Lx holds
+    (each x adds an independent term).  Returns (extrapolated seconds per
+    build, wall seconds of the sample itself)."""
     from oracle import mgw_oracle as orc
 
-    nocc = shape.nocc
+    nocc, naux, nmo = shape.nocc, shape.naux, shape.nmo
+    nx = Lx.shape[2]
     D = orc.energy_differences(eps, nocc)
-    Lov = orc.particle_hole_block(L, nocc)
-    rows = np.linspace(0, shape.naux - 1, resp_rows).astype(int)
+    rows = np.linspace(0, naux - 1, resp_rows).astype(int)
     t0 = time.perf_counter()
     Wr = orc.tda_response_moments(Lov, D, shape.nmom, rows=rows)
-    t_resp = (time.perf_counter() - t0) * shape.naux / resp_rows
-    # a full-shape W for the Sigma timing (values do not change the cost)
-    W = np.zeros((shape.nmom, shape.naux, shape.naux))
+    t_resp = time.perf_counter() - t0
+    # a full-shape W for the Sigma timing (the values do not change the cost)
+    W = np.zeros((shape.nmom, naux, naux))
     W[:, rows, :] = Wr
-    ts = []
-    for r in sig_rows:
-        t0 = time.perf_counter()
-        orc.sigma_moments(eps, nocc, L, W, rows=list(range(r)))
-        ts.append(time.perf_counter() - t0)
-    b = (ts[1] - ts[0]) / (sig_rows[1] - sig_rows[0])
-    a = ts[0] - b * sig_rows[0]
-    t_sig = a + b * shape.nmo
-    cores = os.cpu_count()
-    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
-        if os.environ.get(var, "").isdigit():
-            cores = int(os.environ[var])
-    sample = (f"TDA response for {resp_rows}/{shape.naux} aux rows (x{shape.naux / resp_rows:.0f}) + Sigma moments "
-              f"for {sig_rows[0]} and {sig_rows[1]} of {shape.nmo} orbital rows (linear fit to {shape.nmo})")
-    return t_resp + t_sig, cores, sample
+    t0 = time.perf_counter()
+    orc.sigma_moments(eps[:nx], min(nocc, nx), Lx, W)
+    t_sig = time.perf_counter() - t0
+    return t_resp * naux / resp_rows + t_sig * nmo / nx, t_resp + t_sig
+
+
+def sample_text(shape, resp_rows, nx):
+    return (f"TDA response for {resp_rows} of {shape.naux} aux rows (x{shape.naux / resp_rows:.4g}) + Sigma moments "
+            f"of all {shape.nmo} orbital rows over {nx} of {shape.nmo} Green's-function orbitals x "
+            f"(x{shape.nmo / nx:.4g}), scaled to one Sigma-moment build")
+
+
+def run_oracle_child(args):
+    """--oracle-child: one timed oracle sample in a process whose BLAS thread
+    count was fixed by its environment before numpy loaded; prints JSON."""
+    shape, seed = mgw_inputs.workload(args.workload)
+    threads = args.oracle_child
+    resp_rows, nx = sample_plan(shape, threads)
+    eps, Lov, Lx = sample_inputs(shape, seed, nx)
+    scaled, wall = oracle_sample(shape, eps, Lov, Lx, resp_rows)
+    print(json.dumps({"value": scaled, "wall_s": wall, "threads": threads,
+                      "sample": sample_text(shape, resp_rows, nx)}), flush=True)
+    return 0
+
+
+def cpu_baseline(workload):
+    """The oracle on the host cores, single-threaded and on every core: each
+    in a child process whose OpenBLAS/OpenMP thread counts are set in its
+    environment (so the count is the one used, not a default)."""
+    cores = os.cpu_count() or 1
+    out = {}
+    for threads in (cores, 1):
+        env = dict(os.environ)
+        for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+            env[var] = str(threads)
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--workload", workload, "--oracle-child",
+                            str(threads)], capture_output=True, text=True, env=env, timeout=900)
+        if r.returncode != 0:
+            out[threads] = None
+            continue
+        out[threads] = json.loads(r.stdout.strip().splitlines()[-1])
+    allc, one = out.get(cores), out.get(1)
+    if allc is None:
+        return None
+    return {"value": allc["value"], "unit": "s", "cores": cores, "kind": "oracle", "extrapolated": True,
+            "sample": allc["sample"], "sample_wall_s": allc["wall_s"],
+            "single_thread": None if one is None else {"value": one["value"], "sample": one["sample"],
+                                                       "sample_wall_s": one["wall_s"]}}
 
 
 # ---------------------------------------------------------------------------- reference arm
 
 
 def run_reference(args):
+    """The oracle as it stands on the host cores (every core: numpy's BLAS
+    default), each step one bounded sample of the workload, its time scaled
+    to one Sigma-moment build (value, extrapolated); ms_per_step is the wall
+    time of the sample itself."""
     rank = env_int("RANK", 0)
     if rank != 0:
         return 0
     shape, seed = mgw_inputs.workload(args.workload)
-    eps, L = mgw_inputs.system(shape, seed)
-    vals = []
+    cores = os.cpu_count() or 1
+    resp_rows, nx = sample_plan(shape, cores)
+    eps, Lov, Lx = sample_inputs(shape, seed, nx)
+    vals, walls = [], []
     for i in range(args.warmup + args.steps):
-        v, cores, sample = oracle_sample(shape, eps, L)
+        v, wall = oracle_sample(shape, eps, Lov, Lx, resp_rows)
         if i >= args.warmup:
             vals.append(v)
+            walls.append(wall)
     value = statistics.mean(vals)
+    sample = sample_text(shape, resp_rows, nx)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(walls) * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "extrapolated": True,
         "config": {"workload": args.workload, "nocc": shape.nocc, "nvir": shape.nvir, "naux": shape.naux,
                    "nmom_max": shape.nmom_max, "screening": "tda"},
-        "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle", "extrapolated": True,
+                         "threads": "numpy BLAS default (all cores)", "sample": sample,
+                         "sample_wall_s": statistics.mean(walls)},
         "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -262,12 +346,40 @@ def job_seconds_per_build(slowest_rank_seconds, steps, world):
 
 # ---------------------------------------------------------------------------- GPU arm
 
+PRECISIONS = {"fp64": 0, "fp64_tc": 2, "mixed": 3}  # mgw_precision values
+DIGIT_PRODUCTS = {"fp64_tc": 28, "mixed": 13}       # BF16 digit products per product (ozaki.h levels <= 8)
+Y_KERNEL = {"fp64": "sigma_y_binomial", "fp64_tc": "sigma_y_binomial_tc", "mixed": "sigma_y_binomial_tc"}
+
+
+def fp64_units_rate(h, o64, shape_name="g0w0-nmo400-naux1600"):
+    """GFLOP/s of the FP64-unit Sigma-moment build (response + Sigma), timed
+    with CUDA events on the 400-orbital workload (the path is bound by the
+    FP64 pipe, so its time scales with its flops)."""
+    import torch
+
+    shape, seed = mgw_inputs.workload(shape_name)
+    eps_np, L_np = mgw_inputs.system(shape, seed)
+    eps, L = torch.from_numpy(eps_np).cuda(), torch.from_numpy(L_np).cuda()
+    nocc, nvir, naux, nmom = shape.nocc, shape.nvir, shape.naux, shape.nmom
+    stream = torch.cuda.current_stream()
+    Lov = h.mgw_extract_ov(nocc, nvir, L)
+    W = h.mgw_response_moments(o64, nocc, nvir, naux, nmom, eps, Lov)
+    h.mgw_sigma_moments(o64, nocc, nvir, naux, nmom, eps, L, W)  # warm-up
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    h.mgw_response_moments(o64, nocc, nvir, naux, nmom, eps, Lov, W)
+    h.mgw_sigma_moments(o64, nocc, nvir, naux, nmom, eps, L, W)
+    b.record(stream)
+    b.synchronize()
+    t = a.elapsed_time(b) / 1e3
+    return sum(work_flops(shape)) / t / 1e9, t, shape_name
+
 
 def run_gpu(args):
     import torch
     import torch.distributed as dist
 
-    from paper_2504_17439_gb300 import build, driver, mgw
+    from paper_2504_17439_gb300 import build, mgw
 
     rank, world, local = env_int("RANK", 0), env_int("WORLD_SIZE", 1), env_int("LOCAL_RANK", 0)
     torch.cuda.set_device(local)
@@ -280,32 +392,39 @@ def run_gpu(args):
     nblk = shape.nmom_max + 1
     eps_h = torch.from_numpy(eps_np).pin_memory()
     L_h = torch.from_numpy(L_np).pin_memory()
+    del L_np
     eps = eps_h.cuda()
     L = L_h.cuda()
     stream = torch.cuda.current_stream()
     h = mgw.Handle(local, stream)
     o = mgw.options(screening=mgw.MGW_TDA if args.screening == "tda" else mgw.MGW_RPA,
-                    precision=mgw.MGW_FP64 if args.precision == "fp64" else mgw.MGW_FP64_TC)
-    tc = args.precision == "fp64_tc"
-    ykern = "sigma_y_binomial_tc" if tc else "sigma_y_binomial"
+                    precision=PRECISIONS[args.precision])
+    tc = args.precision != "fp64"
+    ykern = Y_KERNEL[args.precision]
     Lov = torch.empty((naux, nocc * nvir), dtype=torch.float64, device="cuda")
     W = torch.empty((nmom, naux, naux), dtype=torch.float64, device="cuda")
     sh = torch.empty((nmom, nmo, nmo), dtype=torch.float64, device="cuda")
     sp = torch.empty_like(sh)
     fock = torch.diag(eps).contiguous()
 
-    def step(opts=o):
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    def sigma_build(opts=o):  # the timed step: one Sigma-moment build (A1-A8)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         ev[0].record(stream)
         h.mgw_extract_ov(nocc, nvir, L, Lov)
         h.mgw_response_moments(opts, nocc, nvir, naux, nmom, eps, Lov, W)
         h.mgw_sigma_moments(opts, nocc, nvir, naux, nmom, eps, L, W, sh, sp)
         ev[1].record(stream)
+        return ev
+
+    def post_sigma(opts=o):  # block Lanczos of both sectors and the QP solve (A9-A10), once
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
         ch, ah, bh, rh = h.mgw_block_lanczos(opts, nmo, nmom, sh)
         cp, ap, bp, rp = h.mgw_block_lanczos(opts, nmo, nmom, sp)
         qp = h.mgw_qp_solve(opts, nmo, nblk, rh, rp, fock, (ch, ah, bh), (cp, ap, bp), 0.0, 2.0 * nocc)
-        ev[2].record(stream)
-        return ev, qp
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) / 1e3, qp
 
     def barrier():
         torch.cuda.synchronize()
@@ -314,7 +433,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
 
     for _ in range(args.warmup):
-        step()
+        sigma_build()
     barrier()
     launches0 = h.launches
     h.profile(True)
@@ -323,16 +442,13 @@ def run_gpu(args):
     barrier()
     t_wall = time.perf_counter()
     torch.cuda.cudart().cudaProfilerStart()  # a profiler started with capture off records this region only
-    outs = [step() for _ in range(args.steps)]
-    recs = [ev for ev, _ in outs]
-    qp_last = outs[-1][1]
+    recs = [sigma_build() for _ in range(args.steps)]
     barrier()
     torch.cuda.cudart().cudaProfilerStop()
     t_wall = time.perf_counter() - t_wall
     clk = clocks.stop()
     launches = h.launches - launches0
-    build_s = [a.elapsed_time(b) / 1e3 for a, b, _ in recs]
-    step_s = [a.elapsed_time(c) / 1e3 for a, _, c in recs]
+    build_s = [a.elapsed_time(b) / 1e3 for a, b in recs]
     ny, ty_ms = h.profile_query(ykern)
 
     def both(name):  # FP64-unit and tensor-core variants of a stage
@@ -342,21 +458,27 @@ def run_gpu(args):
     n2, t2_ms = both("sigma_gemm2")
     nw, tw_ms = both("w_gemm")
     nt, tt_ms = both("t_update")
-    slice_ms = {nm: h.profile_query(nm)[1] for nm in ("slice_rows", "slice_grouped", "slice_cols", "slice_gather")}
+    slice_ms = {nm: h.profile_query(nm)[1] for nm in ("slice_rows", "slice_grouped", "slice_gather",
+                                                       "slice_gather_grid", "global_exponent")}
     h.profile(False)
+    post_s, qp = post_sigma()
     resp_f, y_f, g2_f = work_flops(shape)
-    # per launch of the dominant kernel: its share of the Y-stage flops (on the
-    # tensor-core path the arithmetic is the 28 BF16 digit products)
-    y_per_launch = y_f * args.steps / max(ny, 1) * (DIGIT_PRODUCTS if tc else 1)
+    # the dominant kernel, per launch: its share of the method's Y-stage flops
+    # (2 nmom naux^2 nmo^2 per build) over its CUDA-event time
+    y_per_launch = y_f * args.steps / max(ny, 1)
     y_avg_s = ty_ms / 1e3 / max(ny, 1)
     achieved = y_per_launch / y_avg_s / 1e9 if ny else None
     peaks = measured_peaks()
     if tc:
         peak = peaks.get("bf16_tflops_sustained", 1700.0) * 1e3
+        prods = DIGIT_PRODUCTS[args.precision]
         roofline = {"kernel": ykern, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
                     "frac": achieved / peak if achieved else None,
                     "traffic": measured_traffic(args.workload, args.precision),
-                    "fp64_equivalent_gflops": achieved / DIGIT_PRODUCTS if achieved else None,
+                    "flops": "method flops 2 nmom naux^2 nmo^2 per build (not the BF16 digit products)",
+                    "bf16_products_per_flop": prods,
+                    "bf16_product_gflops": achieved * prods if achieved else None,
+                    "bf16_product_frac": achieved * prods / peak if achieved else None,
                     "peak_source": "bf16_tflops_sustained of measured (MEASURED_PEAKS.json)" if peaks
                     else "sustained bf16 of fallback"}
     else:
@@ -364,15 +486,19 @@ def run_gpu(args):
                     "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS if achieved else None, "traffic": None,
                     "peak_source": "nominal FP64 rate (profiling recipe table), of fallback"}
 
-    # end to end through the C ABI with host buffers
+    # end to end through the C ABI with host buffers: H2D of eps and L, the
+    # build, D2H of both Sigma tensors, per step (a warm-up and then
+    # min(steps, 2) timed steps: each moves all of L)
     sh_h = torch.empty(sh.shape, dtype=torch.float64).pin_memory()
     sp_h = torch.empty(sp.shape, dtype=torch.float64).pin_memory()
-    e2e = []
-    for i in range(args.warmup + args.steps):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e, h2d = [], []
+    n_e2e = min(args.steps, 2)
+    for i in range(1 + n_e2e):
+        a, c, b = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         a.record(stream)
         eps.copy_(eps_h, non_blocking=True)
         L.copy_(L_h, non_blocking=True)
+        c.record(stream)
         h.mgw_extract_ov(nocc, nvir, L, Lov)
         h.mgw_response_moments(o, nocc, nvir, naux, nmom, eps, Lov, W)
         h.mgw_sigma_moments(o, nocc, nvir, naux, nmom, eps, L, W, sh, sp)
@@ -380,60 +506,76 @@ def run_gpu(args):
         sp_h.copy_(sp, non_blocking=True)
         b.record(stream)
         b.synchronize()
-        if i >= args.warmup:
+        if i >= 1:
             e2e.append(a.elapsed_time(b) / 1e3)
+            h2d.append(a.elapsed_time(c) / 1e3)
+    h2d_bytes = int(L_h.numel() * 8 + eps_h.numel() * 8)
 
-    # the plain FP64 GPU path on the same system, once, outside the timed
-    # region: its Sigma-build time and the largest QP-energy difference
-    fp64_path = None
+    # the FP64-accurate tensor-core path (28 digit products) on the same
+    # system, once, outside the timed region: its build time and the largest
+    # QP-energy difference; and the FP64-unit rate, from which the FP64-unit
+    # build of this workload is estimated
+    compare = None
     if tc and not args.no_compare:
+        compare = {}
+        if args.precision == "mixed":
+            otc = mgw.options(screening=o.screening, precision=mgw.MGW_FP64_TC)
+            ev = sigma_build(otc)
+            ev[1].synchronize()
+            t_tc = ev[0].elapsed_time(ev[1]) / 1e3
+            post_tc, qp_tc = post_sigma(otc)
+            dqp = float((qp["eps_qp"] - qp_tc["eps_qp"]).abs().max())
+            compare["fp64_tc_path"] = {"sigma_build_s": t_tc, "runs": 1, "speedup_sigma_build": t_tc / statistics.mean(build_s),
+                                       "qp_max_abs_diff_meV": dqp * 27211.386245988}
         o64 = mgw.options(screening=o.screening, precision=mgw.MGW_FP64)
-        step(o64)
-        torch.cuda.synchronize()
-        ev64, qp64 = step(o64)
-        torch.cuda.synchronize()
-        t64 = ev64[0].elapsed_time(ev64[1]) / 1e3
-        dqp = float((qp_last["eps_qp"] - qp64["eps_qp"]).abs().max())
-        fp64_path = {"sigma_build_s": t64, "full_step_s": ev64[0].elapsed_time(ev64[2]) / 1e3,
-                     "speedup_sigma_build": t64 / statistics.mean(build_s),
-                     "qp_max_abs_diff_meV": dqp * 27211.386245988}
+        rate, t_small, name = fp64_units_rate(h, o64)
+        est = (resp_f + y_f + g2_f) / (rate * 1e9)
+        compare["fp64_units_path"] = {"estimated": args.workload != name, "gflops": rate,
+                                      "measured_on": name, "measured_s": t_small,
+                                      "sigma_build_s": est if args.workload != name else t_small,
+                                      "speedup_sigma_build": est / statistics.mean(build_s)}
 
     total_build = ranks_max(sum(build_s), world, "cuda")
-    total_step = ranks_max(sum(step_s), world, "cuda")
     total_e2e = ranks_max(sum(e2e), world, "cuda")
-    builds = args.steps * world
     value = job_seconds_per_build(total_build, args.steps, world)
     line = None
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_step / builds * 1e3, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16 digit products -> f64" if tc else "f64", "data": "synthetic",
+            "warmup": args.warmup, "ms_per_step": total_build / (args.steps * world) * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp64_tc": "bf16 digit products -> f64",
+                      "mixed": "bf16 digit products -> f64 (L as bf16 hi/lo on one grid)"}[args.precision],
+            "data": "synthetic",
+            "timed_step": "one Sigma-moment build (particle-hole block, response moments, Sigma moments); "
+                          "block Lanczos and the QP solve run once after the timed region (post_sigma_s)",
             "config": {"workload": args.workload, "nocc": nocc, "nvir": nvir, "naux": naux,
                        "nmom_max": shape.nmom_max, "screening": args.screening, "precision": args.precision,
                        "l2": "inputs larger than L2 (L is %.2f GB)" % (L.numel() * 8 / 1e9)},
-            "stages_s": {"sigma_build": statistics.mean(build_s), "full_step": statistics.mean(step_s),
+            "stages_s": {"sigma_build": statistics.mean(build_s),
                          "w_gemm": tw_ms / 1e3 / args.steps, "t_update": tt_ms / 1e3 / args.steps,
                          ykern: ty_ms / 1e3 / args.steps, "sigma_gemm2": t2_ms / 1e3 / args.steps,
                          **{k: v / 1e3 / args.steps for k, v in slice_ms.items() if v}},
+            "post_sigma_s": post_s,
+            "full_step_s": statistics.mean(build_s) + post_s,
             "gflops_sigma_build": (resp_f + y_f + g2_f) / statistics.mean(build_s) / 1e9,
             "roofline": roofline,
-            "e2e": {"value": total_e2e / builds, "unit": "s",
-                    "h2d_bytes_per_step": int(L_h.numel() * 8 + eps_h.numel() * 8),
-                    "d2h_bytes_per_step": int(2 * sh.numel() * 8)},
+            "e2e": {"value": total_e2e / (len(e2e) * world), "unit": "s", "steps": len(e2e),
+                    "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": int(2 * sh.numel() * 8),
+                    "h2d_gbs": h2d_bytes / statistics.mean(h2d) / 1e9},
             "gpu_launches": launches,
-            "fp64_path": fp64_path,
+            "compare": compare,
             "clocks": clk,
             "wall_s": t_wall,
         }
-        if world == 1 and not args.no_cpu_baseline:
-            v, cores, sample = oracle_sample(shape, eps_np, L_np)
-            line["cpu_baseline"] = {"value": v, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample}
-        print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
     h.close()
+    del L, W, Lov
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args.workload)
+        print(json.dumps(line), flush=True)
     return 0
 
 
@@ -671,8 +813,10 @@ def main():
     ap.add_argument("--impl", default="mgw", choices=["mgw", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(mgw_inputs.WORKLOADS))
     ap.add_argument("--screening", default="tda", choices=["tda", "rpa"])
-    ap.add_argument("--precision", default="fp64_tc", choices=["fp64", "fp64_tc"],
-                    help="fp64_tc: the FP64-accurate digit-sliced tensor-core path (default); fp64: FP64 units")
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "fp64_tc", "mixed"],
+                    help="mixed: L as a BF16 hi/lo split on one grid, 13 exact digit products (default); "
+                         "fp64_tc: the FP64-accurate digit-sliced path (28); fp64: FP64 units")
+    ap.add_argument("--oracle-child", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the one-off plain FP64 comparison run")
     ap.add_argument("--batched", type=int, default=0, help="uneven batch of N systems instead of one system")
@@ -680,6 +824,8 @@ def main():
     ap.add_argument("--fsgw-nmo", default="60,100", help="orbital range of the fsGW systems, lo,hi")
     ap.add_argument("--extras", action="store_true", help="time the next rows: NAF compression, spectral function")
     args = ap.parse_args()
+    if args.oracle_child:
+        return run_oracle_child(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.batched:

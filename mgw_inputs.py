@@ -18,8 +18,10 @@ Coulomb integrals (pq|rs) = sum_Q L[Q,p,q] L[Q,r,s] is (Eq. 13).
 """
 from __future__ import annotations
 
+import concurrent.futures
 import dataclasses
 import math
+import os
 
 import numpy as np
 
@@ -82,12 +84,34 @@ def df_slab(q: int, naux: int, nmo: int, seed: int) -> np.ndarray:
     return (0.1 / math.sqrt(naux)) * 0.5 * (g + g.T)
 
 
-def df_tensor(naux: int, nmo: int, seed: int, out: np.ndarray | None = None) -> np.ndarray:
-    """L[naux][nmo][nmo] in float64 (row-major)."""
+def df_tensor(naux: int, nmo: int, seed: int, out: np.ndarray | None = None, workers: int = 0) -> np.ndarray:
+    """L[naux][nmo][nmo] in float64 (row-major).  Slabs have streams of their
+    own, so they are drawn on `workers` threads (0: one per core for tensors
+    above 2^26 elements) with the same values as one thread."""
     if out is None:
         out = np.empty((naux, nmo, nmo), dtype=np.float64)
-    for q in range(naux):
+
+    def fill(q):
         out[q] = df_slab(q, naux, nmo, seed)
+    if workers == 0:
+        workers = (os.cpu_count() or 1) if naux * nmo * nmo > (1 << 26) else 1
+    if workers <= 1:
+        for q in range(naux):
+            fill(q)
+    else:
+        with concurrent.futures.ThreadPoolExecutor(max_workers=workers) as ex:
+            list(ex.map(fill, range(naux)))
+    return out
+
+
+def sym_matrices(count: int, n: int, seed: int, stream: int = 0x5E3) -> np.ndarray:
+    """count symmetric n x n matrices (G + G^T) / (2 sqrt(n)), G ~ N(0, 1):
+    generic stand-ins for an aux-basis moment stack when a stage is tested
+    on its own."""
+    out = np.empty((count, n, n))
+    for t in range(count):
+        g = _rng(seed, stream + t).standard_normal((n, n))
+        out[t] = (g + g.T) / (2.0 * math.sqrt(n))
     return out
 
 

@@ -440,6 +440,28 @@ def naf_compress(L: np.ndarray, nocc: int, eps_naf: float = 1e-5, pairs: str = "
 
 
 # ----------------------------------------------------------------------------
+# Input rounding of the mixed-precision mode (not in the paper)
+
+
+def fixed_point_grid(X, bits=16, ref_max=None):
+    """X rounded to one fixed-point grid for the whole tensor: with e the
+    exponent for which max |X| < 2^(e-1) (e = floor(log2 max|X|) + 2), every
+    element becomes the nearest multiple of 2^(e-bits), ties away from zero.
+    This is the tensor the mixed-precision mode contracts in place of X (its
+    two BF16 digits hold exactly these values); the method's moments are then
+    computed for it without further rounding.  ref_max (default max |X|)
+    sets the grid, so a part of a tensor can be rounded on the whole tensor's
+    grid.  Not in the paper: the paper's arithmetic is FP64 throughout."""
+    X = np.asarray(X, dtype=np.float64)
+    m = ref_max if ref_max is not None else (float(np.abs(X).max()) if X.size else 0.0)
+    if m == 0.0:
+        return X.copy()
+    e = math.frexp(m)[1] + 1  # m = f 2^k with 1/2 <= f < 1: floor(log2 m) = k - 1
+    unit = math.ldexp(1.0, e - bits)
+    return np.sign(X) * np.floor(np.abs(X) / unit + 0.5) * unit
+
+
+# ----------------------------------------------------------------------------
 # Drivers
 
 

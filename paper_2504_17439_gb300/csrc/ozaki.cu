@@ -15,12 +15,9 @@ __device__ __forceinline__ int row_exponent(double mx) {
   return mx > 0.0 ? ilogb(mx) + 2 : 0;
 }
 
-// digits of x 2^-e: balanced base-256, d_s stored as bf16(d_s 2^-8(s-1)).
-// Integer arithmetic only: X = round(x 2^(56-e)) from the IEEE fields
-// (|X| < 2^55), then d_7, ..., d_2 in [-128, 127] from the low end and
-// d_1 = what is left (|d_1| <= 128), so x 2^-e = sum_s d_s 2^-8s to within
-// half a unit of 2^-56.
-__device__ __forceinline__ void digits_of(double x, int e, __nv_bfloat16 (&d)[kSlices]) {
+// X = round(x 2^(bits - e)) from the IEEE fields, integer arithmetic only
+// (nearest, ties away from zero); |X| < 2^(bits-1) when |x| < 2^(e-1)
+__device__ __forceinline__ long long fixed_of(double x, int e, int bits) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const int bexp = (int)((b >> 52) & 0x7FF);
   unsigned long long m = b & ((1ull << 52) - 1);
@@ -31,19 +28,28 @@ __device__ __forceinline__ void digits_of(double x, int e, __nv_bfloat16 (&d)[kS
     m |= 1ull << 52;
     ex = bexp - 1075;
   }
-  const int sh = ex + 56 - e;
+  const int sh = ex + bits - e;
   long long X;
   if (sh >= 0) {
-    X = (long long)(m << sh);  // sh <= 2 because |x| < 2^(e-1)
+    X = (long long)(m << sh);  // sh <= 2 because |x| < 2^(e-1) and bits <= 56
   } else if (sh > -60) {
     const int r = -sh;
-    X = (long long)((m >> r) + ((m >> (r - 1)) & 1ull));  // nearest, ties away from zero
+    X = (long long)((m >> r) + ((m >> (r - 1)) & 1ull));
   } else {
     X = 0;
   }
-  if (b >> 63) X = -X;
+  return (b >> 63) ? -X : X;
+}
+
+// NS digits of x 2^-e: balanced base-256, d_s stored as bf16(d_s 2^-8(s-1)).
+// X = round(x 2^(8 NS - e)) (|X| < 2^(8 NS - 1)), then d_NS, ..., d_2 in
+// [-128, 127] from the low end and d_1 = what is left (|d_1| <= 128), so
+// x 2^-e = sum_s d_s 2^-8s to within half a unit of 2^-8NS.
+template <int NS>
+__device__ __forceinline__ void digits_of(double x, int e, __nv_bfloat16 (&d)[NS]) {
+  long long X = fixed_of(x, e, 8 * NS);
 #pragma unroll
-  for (int s = kSlices - 1; s >= 1; --s) {
+  for (int s = NS - 1; s >= 1; --s) {
     const int dv = (int)((X + 128) & 255) - 128;
     X = (X - dv) >> 8;
     d[s] = __float2bfloat16_rn(__int2float_rn(dv) * __int_as_float((127 - 8 * s) << 23));
@@ -66,40 +72,108 @@ struct RowsGrouped {
   }
 };
 
-// one warp per row of a row-major source (a null row slices as zero)
-template <class Rows>
-__global__ void k_slice_rows(long rows, long K, Rows src, __nv_bfloat16* dig, long ld, int* exps) {
+// one warp per row of a row-major source (a null row slices as zero); with
+// gexp the exponent is the tensor's grid exponent instead of the row's own
+template <class Rows, int NS>
+__global__ void k_slice_rows(long rows, long K, Rows src, __nv_bfloat16* dig, long ld, int* exps,
+                             const int* gexp) {
   const long r = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (r >= rows) return;
   const double* xr = src.row(r);
-  double mx = 0.0;
-  if (xr)
-    for (long k = lane; k < K; k += 32) mx = fmax(mx, fabs(xr[k]));
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  const int e = row_exponent(mx);
+  int e;
+  if (gexp) {
+    e = *gexp;
+  } else {
+    double mx = 0.0;
+    if (xr)
+      for (long k = lane; k < K; k += 32) mx = fmax(mx, fabs(xr[k]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    e = row_exponent(mx);
+  }
   if (lane == 0) exps[r] = e;
   const long plane = rows * ld;
   for (long k = lane; k < ld; k += 32) {
-    __nv_bfloat16 d[kSlices];
-    digits_of((xr && k < K) ? xr[k] : 0.0, e, d);
+    __nv_bfloat16 d[NS];
+    digits_of<NS>((xr && k < K) ? xr[k] : 0.0, e, d);
 #pragma unroll
-    for (int s = 0; s < kSlices; ++s) dig[s * plane + r * ld + k] = d[s];
+    for (int s = 0; s < NS; ++s) dig[s * plane + r * ld + k] = d[s];
   }
 }
 
 mgw_status slice_rows(mgw_handle* h, long rows, long K, const double* X, long lds, Sliced& out) {
   ProfSpan span(h, "slice_rows");
-  k_slice_rows<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, h->stream>>>(
-      rows, K, RowsPlain{X, lds}, static_cast<__nv_bfloat16*>(out.digits), out.ld, out.exps);
+  if (out.ns != kSlices) return fail(h, MGW_ERR_ARG, "slice_rows: %d-digit planes", out.ns);
+  k_slice_rows<RowsPlain, kSlices><<<(unsigned)((rows * 32 + 255) / 256), 256, 0, h->stream>>>(
+      rows, K, RowsPlain{X, lds}, static_cast<__nv_bfloat16*>(out.digits), out.ld, out.exps, nullptr);
   return check_launch(h, "slice_rows");
+}
+
+mgw_status slice_rows_grid(mgw_handle* h, long rows, long K, const double* X, long lds, const int* gexp,
+                           Sliced& out) {
+  ProfSpan span(h, "slice_rows");
+  if (out.ns != kGridSlices) return fail(h, MGW_ERR_ARG, "slice_rows_grid: %d-digit planes", out.ns);
+  k_slice_rows<RowsPlain, kGridSlices><<<(unsigned)((rows * 32 + 255) / 256), 256, 0, h->stream>>>(
+      rows, K, RowsPlain{X, lds}, static_cast<__nv_bfloat16*>(out.digits), out.ld, out.exps, gexp);
+  return check_launch(h, "slice_rows_grid");
 }
 
 mgw_status slice_grouped(mgw_handle* h, int nmom, int PB, int naux, const double* W, Sliced& out) {
   ProfSpan span(h, "slice_grouped");
-  k_slice_rows<<<(unsigned)((out.rows * 32 + 255) / 256), 256, 0, h->stream>>>(
-      out.rows, naux, RowsGrouped{W, nmom, PB, naux}, static_cast<__nv_bfloat16*>(out.digits), out.ld, out.exps);
+  if (out.ns != kSlices) return fail(h, MGW_ERR_ARG, "slice_grouped: %d-digit planes", out.ns);
+  k_slice_rows<RowsGrouped, kSlices><<<(unsigned)((out.rows * 32 + 255) / 256), 256, 0, h->stream>>>(
+      out.rows, naux, RowsGrouped{W, nmom, PB, naux}, static_cast<__nv_bfloat16*>(out.digits), out.ld, out.exps,
+      nullptr);
   return check_launch(h, "slice_grouped");
+}
+
+// max |x| over n elements into *gmax (bit pattern; zeroed by the caller)
+__global__ void k_absmax(long n, const double* __restrict__ X, unsigned long long* gmax) {
+  double m = 0.0;
+  const long stride = (long)gridDim.x * blockDim.x;
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+#pragma unroll 4
+  for (; i < n; i += stride) m = fmax(m, fabs(X[i]));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ double sm[32];
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) atomicMax(gmax, (unsigned long long)__double_as_longlong(m));
+  }
+}
+__global__ void k_grid_exponent(const unsigned long long* gmax, int* gexp) {
+  *gexp = row_exponent(__longlong_as_double((long long)*gmax));
+}
+
+mgw_status global_exponent(mgw_handle* h, long n, const double* X, unsigned long long* gmax, int* gexp) {
+  ProfSpan span(h, "global_exponent");
+  MGW_CUDA(h, cudaMemsetAsync(gmax, 0, sizeof(unsigned long long), h->stream));
+  if (n > 0) {
+    const long blocks = std::min<long>((n + 255) / 256, 152L * 8);
+    k_absmax<<<(unsigned)blocks, 256, 0, h->stream>>>(n, X, gmax);
+    MGW_TRY(check_launch(h, "absmax"));
+  }
+  k_grid_exponent<<<1, 1, 0, h->stream>>>(gmax, gexp);
+  return check_launch(h, "grid_exponent");
+}
+
+// Xr = X rounded to the grid 2^(ex - 8 kGridSlices): the value its digits carry
+__global__ void k_round_to_grid(long n, const double* __restrict__ X, const int* __restrict__ gexp, double* Xr) {
+  const int e = *gexp;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const long long q = fixed_of(X[i], e, 8 * kGridSlices);
+    // |q| < 2^15: exact in a double, and the power of two scales it exactly
+    Xr[i] = ldexp((double)q, e - 8 * kGridSlices);
+  }
+}
+
+mgw_status round_to_grid(mgw_handle* h, long n, const double* X, const int* gexp, double* Xr) {
+  if (n <= 0) return MGW_OK;
+  k_round_to_grid<<<(unsigned)std::min<long>((n + 255) / 256, 152L * 16), 256, 0, h->stream>>>(n, X, gexp, Xr);
+  return check_launch(h, "round_to_grid");
 }
 
 // Gathered sources with rows contiguous in memory: element (r, k) sits at
@@ -146,17 +220,19 @@ __global__ void k_gather_rowmax(long rows, long K, const double* __restrict__ X,
 }
 
 // pass 2: one 32-row x 64-k tile per CTA; digits staged in shared memory and
-// written along k (128 B per row and digit plane)
+// written along k (128 B per row and digit plane).  With gexp every row takes
+// the tensor's grid exponent (no max pass).
+template <int NS>
 __global__ void k_gather_digits(long rows, long K, const double* __restrict__ X, Gather g,
-                                const unsigned long long* __restrict__ rmax, __nv_bfloat16* dig, long ld,
-                                int* exps) {
-  __shared__ __align__(4) __nv_bfloat16 sd[kSlices][32][66];
+                                const unsigned long long* __restrict__ rmax, const int* __restrict__ gexp,
+                                __nv_bfloat16* dig, long ld, int* exps) {
+  __shared__ __align__(4) __nv_bfloat16 sd[NS][32][66];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const long r0 = blockIdx.x * 32L, r = r0 + lane;
   const long k0 = blockIdx.y * 64L;
   int e = 0;
   if (r < rows) {
-    e = row_exponent(__longlong_as_double((long long)rmax[r]));
+    e = gexp ? *gexp : row_exponent(__longlong_as_double((long long)rmax[r]));
     if (blockIdx.y == 0) exps[r] = e;
   }
   const double* xr = r < rows ? X + (r / g.rdiv) * g.rhi + (r % g.rdiv) * g.rlo : X;
@@ -166,14 +242,14 @@ __global__ void k_gather_digits(long rows, long K, const double* __restrict__ X,
     const long k = k0 + kk;
     const double x = (r < rows && k < K) ? xr[kw.off()] : 0.0;
     kw.step(8);
-    __nv_bfloat16 d[kSlices];
-    digits_of(x, e, d);
+    __nv_bfloat16 d[NS];
+    digits_of<NS>(x, e, d);
 #pragma unroll
-    for (int s = 0; s < kSlices; ++s) sd[s][lane][kk] = d[s];
+    for (int s = 0; s < NS; ++s) sd[s][lane][kk] = d[s];
   }
   __syncthreads();
   const long plane = rows * ld;
-  for (int i = threadIdx.x; i < kSlices * 32 * 32; i += 256) {  // 32-bit words: two k per word
+  for (int i = threadIdx.x; i < NS * 32 * 32; i += 256) {  // 32-bit words: two k per word
     const int s = i / (32 * 32), rr = (i / 32) % 32, kp = (i % 32) * 2;
     if (r0 + rr < rows && k0 + kp < ld)
       *reinterpret_cast<uint32_t*>(dig + s * plane + (r0 + rr) * ld + k0 + kp) =
@@ -183,6 +259,7 @@ __global__ void k_gather_digits(long rows, long K, const double* __restrict__ X,
 
 mgw_status slice_gather(mgw_handle* h, long rows, long K, const double* X, const Gather& g, Sliced& out) {
   ProfSpan span(h, "slice_gather");
+  if (out.ns != kSlices) return fail(h, MGW_ERR_ARG, "slice_gather: %d-digit planes", out.ns);
   if (rows <= 0) return MGW_OK;
   if (out.ld == 0) {  // K = 0: no digits, zero exponents
     MGW_CUDA(h, cudaMemsetAsync(out.exps, 0, sizeof(int) * rows, h->stream));
@@ -198,9 +275,24 @@ mgw_status slice_gather(mgw_handle* h, long rows, long K, const double* X, const
     k_gather_rowmax<<<dim3((unsigned)gx, (unsigned)ksplit), 256, 0, h->stream>>>(rows, K, X, g, kper, out.rmax);
     MGW_TRY(check_launch(h, "gather_rowmax"));
   }
-  k_gather_digits<<<dim3((unsigned)gx, (unsigned)(out.ld / 64)), 256, 0, h->stream>>>(
-      rows, K, X, g, out.rmax, static_cast<__nv_bfloat16*>(out.digits), out.ld, out.exps);
+  k_gather_digits<kSlices><<<dim3((unsigned)gx, (unsigned)(out.ld / 64)), 256, 0, h->stream>>>(
+      rows, K, X, g, out.rmax, nullptr, static_cast<__nv_bfloat16*>(out.digits), out.ld, out.exps);
   return check_launch(h, "gather_digits");
+}
+
+mgw_status slice_gather_grid(mgw_handle* h, long rows, long K, const double* X, const Gather& g, const int* gexp,
+                             Sliced& out) {
+  ProfSpan span(h, "slice_gather_grid");
+  if (out.ns != kGridSlices) return fail(h, MGW_ERR_ARG, "slice_gather_grid: %d-digit planes", out.ns);
+  if (rows <= 0) return MGW_OK;
+  if (out.ld == 0) {
+    MGW_CUDA(h, cudaMemsetAsync(out.exps, 0, sizeof(int) * rows, h->stream));
+    return MGW_OK;
+  }
+  const long gx = (rows + 31) / 32;
+  k_gather_digits<kGridSlices><<<dim3((unsigned)gx, (unsigned)(out.ld / 64)), 256, 0, h->stream>>>(
+      rows, K, X, g, nullptr, gexp, static_cast<__nv_bfloat16*>(out.digits), out.ld, out.exps);
+  return check_launch(h, "gather_digits_grid");
 }
 
 mgw_status slice_cols(mgw_handle* h, long rows, long K, const double* X, long ldx, Sliced& out) {
@@ -209,13 +301,13 @@ mgw_status slice_cols(mgw_handle* h, long rows, long K, const double* X, long ld
 }
 
 mgw_status digit_map(mgw_handle* h, CUtensorMap* map, const Sliced& s, int box_rows) {
-  return tc::make_map_3d(h, map, s.digits, s.ld, s.rows, kSlices, s.ld * 2, s.rows * s.ld * 2, box_rows, 1);
+  return tc::make_map_3d(h, map, s.digits, s.ld, s.rows, s.ns, s.ld * 2, s.rows * s.ld * 2, box_rows, 1);
 }
 
 // bytes of the digit planes + exponents of `rows` x K (in doubles, rounded)
-size_t sliced_doubles(long rows, long K) {
+size_t sliced_doubles(long rows, long K, int ns) {
   const long ld = (K + 63) / 64 * 64;
-  return (size_t)((kSlices * rows * ld * 2 + 7) / 8) + (size_t)((rows * 4 + 7) / 8) + (size_t)rows + 64;
+  return (size_t)((ns * rows * ld * 2 + 7) / 8) + (size_t)((rows * 4 + 7) / 8) + (size_t)rows + 64;
 }
 
 __global__ void k_sum_splits(long count, int nsplit, const double* __restrict__ part, double* out,
@@ -258,13 +350,14 @@ using namespace mgw::oz;
 
 namespace mgw {
 namespace oz {
-void place_sliced(double* mem, long rows, long K, Sliced& s) {
+void place_sliced(double* mem, long rows, long K, Sliced& s, int ns) {
   const long ld = (K + 63) / 64 * 64;
   s.rows = rows;
   s.ld = ld;
+  s.ns = ns;
   s.digits = mem;
-  s.exps = reinterpret_cast<int*>(mem + (kSlices * rows * ld * 2 + 7) / 8);
-  s.rmax = reinterpret_cast<unsigned long long*>(mem + (kSlices * rows * ld * 2 + 7) / 8 + (rows * 4 + 7) / 8);
+  s.exps = reinterpret_cast<int*>(mem + (ns * rows * ld * 2 + 7) / 8);
+  s.rmax = reinterpret_cast<unsigned long long*>(mem + (ns * rows * ld * 2 + 7) / 8 + (rows * 4 + 7) / 8);
 }
 }  // namespace oz
 }  // namespace mgw

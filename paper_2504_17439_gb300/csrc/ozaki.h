@@ -53,6 +53,7 @@ namespace oz {
 constexpr int BM = 128, BN = 96, BK = 64;
 constexpr int kCols = BN / 2;          // output columns per epilogue thread
 constexpr int kSlices = 7;
+constexpr int kGridSlices = 2;        // digits of a tensor sliced on one fixed-point grid (mixed precision)
 constexpr int kExactTop = 7;          // levels 2..7 accumulated exactly
 constexpr int kRegTop = 5;            // levels 2..5 in registers, 6..7 in TMEM
 constexpr int kThreads = 384;
@@ -137,14 +138,34 @@ __device__ __forceinline__ double combine_parts(long long acc, long long a67, fl
   return i64_ldexp(W, E - 24 - sh);
 }
 
-__host__ __device__ inline int chunk_of_level(int l) {  // K chunk (multiple of BK) of an exact level
-  int c = 1024 / (l - 1);
+// The operands may carry different digit counts: SA digits for A, SB for B
+// (SA, SB <= 7).  Level l = s + u then holds the products s <= SA, u <= SB;
+// levels above kLowTop = 8 are dropped (below 2^-64 of the top), so with
+// SA = SB = 7 there are 28 products and with one operand on two digits 13.
+constexpr int kLowTop = kSlices + 1;
+__host__ __device__ constexpr int level_lo(int l, int SB) { return l - SB > 1 ? l - SB : 1; }
+__host__ __device__ constexpr int level_hi(int l, int SA) { return SA < l - 1 ? SA : l - 1; }
+__host__ __device__ constexpr int level_products(int l, int SA, int SB) {
+  return level_hi(l, SA) >= level_lo(l, SB) ? level_hi(l, SA) - level_lo(l, SB) + 1 : 0;
+}
+__host__ __device__ constexpr int digit_products(int SA, int SB) {
+  int n = 0;
+  for (int l = 2; l <= kLowTop; ++l) n += level_products(l, SA, SB);
+  return n;
+}
+// K chunk (multiple of BK) over which an exact level's FP32 sum stays below
+// 2^24: np products of two digits of magnitude <= 2^7 per k
+__host__ __device__ inline int chunk_of_level(int l, int SA, int SB) {
+  int c = 1024 / level_products(l, SA, SB);
   return (c / BK) * BK;
 }
 
 // Walks the (phase, product, K block) sequence every role follows.  A phase
 // is one exact level over one K chunk, or (last) all low levels over all K.
+template <int SA, int SB>
 struct Schedule {
+  static_assert(SA >= 1 && SB >= 1 && SA <= kSlices && SB <= kSlices, "1..7 digits per operand");
+  static_assert(SA + SB >= kLowTop, "every level 2..8 holds at least one product");
   int K;
   int kb_total;
   __device__ Schedule(int K_) : K(K_), kb_total((K_ + BK - 1) / BK) {}
@@ -153,10 +174,10 @@ struct Schedule {
   __device__ void run(F&& f) const {
     int phase = 0;
     for (int l = 2; l <= kExactTop; ++l) {
-      const int cb = chunk_of_level(l) / BK;
+      const int cb = chunk_of_level(l, SA, SB) / BK;
       for (int c0 = 0; c0 < kb_total; c0 += cb) {
         const int c1 = min(kb_total, c0 + cb);
-        const int s_lo = max(1, l - kSlices), s_hi = min(kSlices, l - 1);
+        const int s_lo = level_lo(l, SB), s_hi = level_hi(l, SA);
         bool first = true;
         for (int s = s_lo; s <= s_hi; ++s)
           for (int kb = c0; kb < c1; ++kb) {
@@ -168,21 +189,21 @@ struct Schedule {
       }
     }
     bool first = true;
-    for (int l = kExactTop + 1; l <= kSlices + 1; ++l) {
-      const int s_lo = max(1, l - kSlices), s_hi = min(kSlices, l - 1);
+    for (int l = kExactTop + 1; l <= kLowTop; ++l) {
+      const int s_lo = level_lo(l, SB), s_hi = level_hi(l, SA);
       for (int s = s_lo; s <= s_hi; ++s)
         for (int kb = 0; kb < kb_total; ++kb) {
-          const bool last = (l == kSlices + 1) && (s == s_hi) && (kb == kb_total - 1);
+          const bool last = (l == kLowTop) && (s == s_hi) && (kb == kb_total - 1);
           if (!f(phase, true, 0, s, l - s, kb, first, last)) return;
           first = false;
         }
     }
   }
-  __device__ int items() const { return kSlices * (kSlices + 1) / 2 * kb_total; }  // all 28 products
+  __device__ int items() const { return digit_products(SA, SB) * kb_total; }
   __device__ int phases() const {
     int p = 0;
     for (int l = 2; l <= kExactTop; ++l) {
-      const int cb = chunk_of_level(l) / BK;
+      const int cb = chunk_of_level(l, SA, SB) / BK;
       p += (kb_total + cb - 1) / cb;
     }
     return p + 1;
@@ -197,7 +218,7 @@ struct ARowsPlain {
   }
 };
 
-template <class ALoad, class Epi>
+template <int SA, int SB, class ALoad, class Epi>
 __global__ void __launch_bounds__(kThreads, 1)
 ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
                   const int* __restrict__ ea, const int* __restrict__ eb, int M, int N, int K, int col_band,
@@ -240,7 +261,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
   // split z = blockIdx.y covers k in [k0, k0 + ksplit); its partial result
   // goes where the epilogue puts split z
   const int k0 = (int)blockIdx.y * ksplit;
-  const Schedule sched(min(ksplit, K - k0));
+  const Schedule<SA, SB> sched(min(ksplit, K - k0));
 
   if (threadIdx.x == 0) {
     for (int g = 0; g < kGroups; ++g) {
@@ -415,7 +436,8 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
             }
           }
         }
-        const int nchunks = (sched.kb_total + chunk_of_level(l) / BK - 1) / (chunk_of_level(l) / BK);
+        const int cbl = chunk_of_level(l, SA, SB) / BK;
+        const int nchunks = (sched.kb_total + cbl - 1) / cbl;
         if (++chunk_idx == nchunks) { chunk_idx = 0; ++l_of_phase; }
       } else {
         // last phase: value = 2^(e_i + f_j - 16) (acc 2^-24 + acc67 2^-40 + low).
@@ -462,15 +484,19 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
 
 // ---- host side
 
-struct Sliced {  // digits [kSlices][rows][ld] BF16 + exponents [rows] + row maxima scratch [rows]
+struct Sliced {  // digits [ns][rows][ld] BF16 + exponents [rows] + row maxima scratch [rows]
   void* digits = nullptr;
   int* exps = nullptr;
   unsigned long long* rmax = nullptr;
   long rows = 0, ld = 0;
+  int ns = kSlices;  // digits per element
 };
 
 // slice a row-major FP64 matrix X[rows][K] (row stride lds) -> digits, exponents
 mgw_status slice_rows(mgw_handle* h, long rows, long K, const double* X, long lds, Sliced& out);
+// the same on the tensor's grid (two digits, exponent *gexp for every row)
+mgw_status slice_rows_grid(mgw_handle* h, long rows, long K, const double* X, long lds, const int* gexp,
+                           Sliced& out);
 // slice the stacked moments W[nmom][naux][naux] into grouped rows: result row
 // R = g*128 + t*PB + pl holds W[t][g*PB + pl][:] (zero past nmom*PB or naux)
 mgw_status slice_grouped(mgw_handle* h, int nmom, int PB, int naux, const double* W, Sliced& out);
@@ -481,8 +507,21 @@ mgw_status slice_cols(mgw_handle* h, long rows, long K, const double* X, long ld
 // CTAs take 32 consecutive rows, so rlo = 1 keeps the reads coalesced
 struct Gather { long rdiv, rhi, rlo, kdiv, khi, klo; };
 mgw_status slice_gather(mgw_handle* h, long rows, long K, const double* X, const Gather& g, Sliced& out);
-size_t sliced_doubles(long rows, long K);           // workspace for rows x K digits + exponents
-void place_sliced(double* mem, long rows, long K, Sliced& s);
+// workspace for rows x K elements of ns digits + exponents
+size_t sliced_doubles(long rows, long K, int ns = kSlices);
+void place_sliced(double* mem, long rows, long K, Sliced& s, int ns = kSlices);
+// Fixed-point slicing on one grid for a whole tensor (two digits, the BF16
+// hi/lo split of the mixed precision): ex = the exponent with |x| 2^-ex < 1/2
+// for every element, each element rounded to a multiple of 2^(ex-16) and
+// written as two balanced base-256 digits, every row exponent set to ex.
+// The rounded tensor is the same whatever rows and K the slicing takes, so
+// every product of the path sees one tensor.  global_exponent computes ex
+// into gexp (device) from the max |x| of n elements.
+mgw_status global_exponent(mgw_handle* h, long n, const double* X, unsigned long long* gmax, int* gexp);
+mgw_status slice_gather_grid(mgw_handle* h, long rows, long K, const double* X, const Gather& g, const int* gexp,
+                             Sliced& out);
+// X' = X rounded to that grid (the FP64 values the two digits represent)
+mgw_status round_to_grid(mgw_handle* h, long n, const double* X, const int* gexp, double* Xr);
 // 3D tensor map over digits: (k, row, digit), box (64, box_rows, 1)
 mgw_status digit_map(mgw_handle* h, CUtensorMap* map, const Sliced& s, int box_rows);
 
@@ -517,13 +556,14 @@ inline int best_split(long kept, long K, int sms) {
 // sum of the split buffers: out[i] = (accumulate ? out[i] : 0) + sum_z part[z count + i]
 mgw_status reduce_splits(mgw_handle* h, long count, int nsplit, const double* part, double* out, int accumulate);
 
-template <class ALoad, class Epi>
+// SA, SB: digits of A and B (the tensor maps must hold that many planes)
+template <int SA = kSlices, int SB = kSlices, class ALoad, class Epi>
 mgw_status ozaki_launch(mgw_handle* h, const CUtensorMap& mA, const CUtensorMap& mB, const int* ea,
                         const int* eb, int M, int N, int K, const ALoad& al, const Epi& epi, int* dstatus,
                         const char* what, int nsplit = 1) {
   if (K >= (1 << 24))  // the exact 128-bit combine of the epilogue needs K < 2^24
     return fail(h, MGW_ERR_UNSUPPORTED, "%s: K = %d too large for the digit-sliced GEMM", what, K);
-  auto kern = ozaki_gemm_kernel<ALoad, Epi>;
+  auto kern = ozaki_gemm_kernel<SA, SB, ALoad, Epi>;
   // once per instantiation (thread-safe static initialisation)
   static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
   MGW_CUDA(h, attr);

@@ -12,9 +12,12 @@
 // digit-sliced products on the tensor cores (ozaki.h): V is sliced once as
 // rows (for W = T V^T) and, for TDA, once transposed (for W V); T and W(t)
 // are sliced before each use, and the update's epilogue applies the
-// diagonal term exactly as the FP64 kernel does.  For the RPA the
-// contractions of the eta~(0) quadrature run on the tensor cores as well;
-// the Cholesky solves of each node stay FP64 (cuSOLVER).
+// diagonal term exactly as the FP64 kernel does.  With MGW_MIXED (TDA) V is
+// first rounded to one 16-bit fixed-point grid (V', two digits per element)
+// and the whole recursion runs on V' (T(0) = V' too), so the moments are
+// exactly those of the system with V' at 13 digit products per product.
+// For the RPA the contractions of the eta~(0) quadrature run on the tensor
+// cores as well; the Cholesky solves of each node stay FP64 (cuSOLVER).
 #include "mgw_internal.h"
 #include "ozaki.h"
 #include "tc_gemm.h"
@@ -237,15 +240,21 @@ extern "C" mgw_status mgw_response_moments(mgw_handle* h, const mgw_options* o, 
     return fail(h, MGW_ERR_ARG, "mgw_response_moments: unknown screening %d", o->screening);
   if (o->screening == MGW_RPA && (o->nquad < 2 || o->nquad % 2))
     return fail(h, MGW_ERR_ARG, "mgw_response_moments: nquad must be even and >= 2");
-  if (o->precision != MGW_FP64 && o->precision != MGW_FP64_TC)
+  if (o->precision != MGW_FP64 && o->precision != MGW_FP64_TC && o->precision != MGW_MIXED)
     return fail(h, MGW_ERR_UNSUPPORTED, "mgw_response_moments: precision %d not built", o->precision);
   MGW_CUDA(h, cudaSetDevice(h->device));
   const long ov = (long)nocc * nvir;
   const long na2 = (long)naux * naux;
   const long tsz = (long)naux * ov;
 
-  const bool use_tc = o->screening == MGW_TDA && o->precision == MGW_FP64_TC;
-  const bool rpa_tc = o->screening == MGW_RPA && o->precision == MGW_FP64_TC;
+  const bool any_tc = o->precision == MGW_FP64_TC || o->precision == MGW_MIXED;
+  const bool use_tc = o->screening == MGW_TDA && any_tc;
+  const bool rpa_tc = o->screening == MGW_RPA && any_tc;  // the RPA takes V unrounded in both modes
+  // TDA under MGW_MIXED: the response of V' (V rounded to one 16-bit grid,
+  // two digits): T(0) = V', W(t) = T(t) V'^T, T(t+1) = T(t) D + 2 W(t) V', so
+  // W(t) = V' A'^t V'^T exactly for A' = D + 2 V'^T V'; T and W keep 7 digits
+  const bool mixed = use_tc && o->precision == MGW_MIXED;
+  const int vns = mixed ? oz::kGridSlices : oz::kSlices;
   Arena ar;
   double *D = nullptr, *T0 = nullptr, *T1 = nullptr, *aux = nullptr, *work = nullptr, *mm = nullptr;
   double *vd = nullptr, *vtd = nullptr, *td = nullptr, *wd = nullptr, *st = nullptr;
@@ -264,11 +273,11 @@ extern "C" mgw_status mgw_response_moments(mgw_handle* h, const mgw_options* o, 
       for (int n0 = 0; n0 < naux; n0 += oz::BN) kept += oz::sym_tile_lower(m0, n0, naux) ? 0 : 1;
     w_req = oz::best_split(kept, ov, sms);
     w_nz = oz::split_count(ov, w_req);
-    ar.add(&vd, oz::sliced_doubles(naux, ov));
-    ar.add(&vtd, oz::sliced_doubles(ov, naux));
+    ar.add(&vd, oz::sliced_doubles(naux, ov, vns));
+    ar.add(&vtd, oz::sliced_doubles(ov, naux, vns));
     ar.add(&td, oz::sliced_doubles(naux, ov));
     ar.add(&wd, oz::sliced_doubles(naux, naux));
-    ar.add(&st, 1);
+    ar.add(&st, 3);  // status word; the grid's max |V| and exponent
     if (w_nz > 1) ar.add(&wpart, (size_t)w_nz * na2);
   }
   double *ad = nullptr, *bd = nullptr;
@@ -290,35 +299,50 @@ extern "C" mgw_status mgw_response_moments(mgw_handle* h, const mgw_options* o, 
     int* dstatus = h->defer_status ? h->defer_status : reinterpret_cast<int*>(st);
     if (!h->defer_status) MGW_CUDA(h, cudaMemsetAsync(dstatus, 0, sizeof(int), h->stream));
     oz::Sliced sv, svt, stt, sww;
-    oz::place_sliced(vd, naux, ov, sv);
-    oz::place_sliced(vtd, ov, naux, svt);
+    oz::place_sliced(vd, naux, ov, sv, vns);
+    oz::place_sliced(vtd, ov, naux, svt, vns);
     oz::place_sliced(td, naux, ov, stt);
     oz::place_sliced(wd, naux, naux, sww);
-    MGW_TRY(oz::slice_rows(h, naux, ov, Lov, ov, sv));
-    MGW_TRY(oz::slice_gather(h, ov, naux, Lov, oz::Gather{ov + 1, 0, 1, naux + 1, 0, ov}, svt));
+    const oz::Gather gvt{ov + 1, 0, 1, naux + 1, 0, ov};  // V^T: rows ia, K = Q
+    if (mixed) {
+      int* gexp = reinterpret_cast<int*>(st + 2);
+      MGW_TRY(oz::global_exponent(h, tsz, Lov, reinterpret_cast<unsigned long long*>(st + 1), gexp));
+      MGW_TRY(oz::slice_rows_grid(h, naux, ov, Lov, ov, gexp, sv));
+      MGW_TRY(oz::slice_gather_grid(h, ov, naux, Lov, gvt, gexp, svt));
+      MGW_TRY(oz::round_to_grid(h, tsz, Lov, gexp, T0));  // T(0) = V'
+    } else {
+      MGW_TRY(oz::slice_rows(h, naux, ov, Lov, ov, sv));
+      MGW_TRY(oz::slice_gather(h, ov, naux, Lov, gvt, svt));
+      MGW_CUDA(h, cudaMemcpyAsync(T0, Lov, sizeof(double) * tsz, cudaMemcpyDeviceToDevice, h->stream));
+    }
     CUtensorMap mv, mvt, mt, mw;
     MGW_TRY(oz::digit_map(h, &mv, sv, oz::BN));
     MGW_TRY(oz::digit_map(h, &mvt, svt, oz::BN));
     MGW_TRY(oz::digit_map(h, &mt, stt, oz::BM));
     MGW_TRY(oz::digit_map(h, &mw, sww, oz::BM));
-    MGW_CUDA(h, cudaMemcpyAsync(T0, Lov, sizeof(double) * tsz, cudaMemcpyDeviceToDevice, h->stream));
+    // the two products of an order: B = V (rows Q) or V^T (rows ia), 2 digits under MGW_MIXED
+    auto launch = [&](const CUtensorMap& ma, const CUtensorMap& mb, const int* ea, const int* eb, int M, int N,
+                      int K, auto epi, const char* what, int nsp) {
+      if (mixed)
+        return oz::ozaki_launch<oz::kSlices, oz::kGridSlices>(h, ma, mb, ea, eb, M, N, K, oz::ARowsPlain{}, epi,
+                                                              dstatus, what, nsp);
+      return oz::ozaki_launch(h, ma, mb, ea, eb, M, N, K, oz::ARowsPlain{}, epi, dstatus, what, nsp);
+    };
     for (int n = 0; n < nmom; ++n) {
       double* Wn = Wmom + (long)n * na2;
       MGW_TRY(oz::slice_rows(h, naux, ov, T0, ov, stt));
       if (w_nz == 1) {
-        MGW_TRY((oz::ozaki_launch(h, mt, mv, stt.exps, sv.exps, naux, naux, (int)ov, oz::ARowsPlain{},
-                                  oz::EpiElem<oz::FStoreSym>{oz::FStoreSym{Wn, naux, 0}}, dstatus, "w_gemm_tc")));
+        MGW_TRY(launch(mt, mv, stt.exps, sv.exps, naux, naux, (int)ov,
+                       oz::EpiElem<oz::FStoreSym>{oz::FStoreSym{Wn, naux, 0}}, "w_gemm_tc", 1));
       } else {
-        MGW_TRY((oz::ozaki_launch(h, mt, mv, stt.exps, sv.exps, naux, naux, (int)ov, oz::ARowsPlain{},
-                                  oz::EpiElem<oz::FStoreSym>{oz::FStoreSym{wpart, naux, na2}}, dstatus, "w_gemm_tc",
-                                  w_req)));
+        MGW_TRY(launch(mt, mv, stt.exps, sv.exps, naux, naux, (int)ov,
+                       oz::EpiElem<oz::FStoreSym>{oz::FStoreSym{wpart, naux, na2}}, "w_gemm_tc", w_req));
         MGW_TRY(oz::reduce_splits(h, na2, w_nz, wpart, Wn, 0));
       }
       if (n + 1 < nmom) {
         MGW_TRY(oz::slice_rows(h, naux, naux, Wn, naux, sww));
-        MGW_TRY((oz::ozaki_launch(h, mw, mvt, sww.exps, svt.exps, naux, (int)ov, naux, oz::ARowsPlain{},
-                                  oz::EpiElem<oz::FDiagUpdate>{oz::FDiagUpdate{T0, ov, D, 2.0}}, dstatus,
-                                  "t_update_tc")));
+        MGW_TRY(launch(mw, mvt, sww.exps, svt.exps, naux, (int)ov, naux,
+                       oz::EpiElem<oz::FDiagUpdate>{oz::FDiagUpdate{T0, ov, D, 2.0}}, "t_update_tc", 1));
       }
     }
     return h->defer_status ? MGW_OK : tc::check_tc_status(h, dstatus, "mgw_response_moments");

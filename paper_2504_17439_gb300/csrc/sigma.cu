@@ -16,7 +16,13 @@
 // FP64-accurate digit-sliced GEMM (ozaki.h): W is sliced once in grouped-row
 // order (a 128-row tile holds all nmom orders of PB = 128/nmom aux rows), each
 // x-chunk of L is sliced as its transpose, and the same binomial weighting
-// runs in that kernel's epilogue from shared memory.
+// runs in that kernel's epilogue from shared memory.  With MGW_MIXED both
+// products take L on one fixed-point grid for the whole tensor (two digits, a
+// BF16 hi/lo split: L' = L rounded to a multiple of 2^(e-16), |L| < 2^(e-1))
+// and W, Z on seven digits: 13 digit products instead of 28, every one exact.
+// The result is then the moments of the system whose DF tensor is L' (a
+// consistent moment sequence, which the block Lanczos step needs), computed
+// to FP64 accuracy; L' differs from L by at most 2^-17 of max |L|.
 #include "mgw_internal.h"
 #include "ozaki.h"
 #include "tc_gemm.h"
@@ -176,9 +182,13 @@ extern "C" mgw_status mgw_sigma_moments(mgw_handle* h, const mgw_options* o, int
   if (nocc < 1 || nvir < 1 || naux < 1 || nmom < 1 || nmom > kMaxMom || !eps_G || !L || !Wmom || !sig_hole ||
       !sig_part)
     return fail(h, MGW_ERR_ARG, "mgw_sigma_moments: bad sizes or null pointer");
-  if (o->precision != MGW_FP64 && o->precision != MGW_FP64_TC)
+  if (o->precision != MGW_FP64 && o->precision != MGW_FP64_TC && o->precision != MGW_MIXED)
     return fail(h, MGW_ERR_UNSUPPORTED, "mgw_sigma_moments: precision %d not built", o->precision);
-  const bool tc = o->precision == MGW_FP64_TC;
+  // MGW_MIXED: L enters both products as the same tensor L' (L rounded to one
+  // 16-bit fixed-point grid, two digits); W, Y and Z keep seven digits
+  const bool mixed = o->precision == MGW_MIXED;
+  const bool tc = o->precision == MGW_FP64_TC || mixed;
+  const int lns = mixed ? oz::kGridSlices : oz::kSlices;
   MGW_CUDA(h, cudaSetDevice(h->device));
   const int nmo = nocc + nvir;
   constexpr int BM = 96, BN = 64;
@@ -211,10 +221,10 @@ extern "C" mgw_status mgw_sigma_moments(mgw_handle* h, const mgw_options* o, int
   ar.add(&part, (size_t)std::max(nsplit, nsplit_tc) * nmom * n2);
   if (tc) {
     ar.add(&wdig, oz::sliced_doubles(ngroups_t * 128, naux));
-    ar.add(&ldig, oz::sliced_doubles((long)xc * nmo, naux));
-    ar.add(&adig, oz::sliced_doubles(nmo, (long)xc * naux));          // GEMM2 A: rows p, K = (x, P)
+    ar.add(&ldig, oz::sliced_doubles((long)xc * nmo, naux, lns));
+    ar.add(&adig, oz::sliced_doubles(nmo, (long)xc * naux, lns));          // GEMM2 A: rows p, K = (x, P)
     ar.add(&zdig, oz::sliced_doubles((long)nmom * nmo, (long)xc * naux));  // GEMM2 B: rows (n, q)
-    ar.add(&st, 1);
+    ar.add(&st, 3);  // status word; the grid's max |L| and exponent
   }
   MGW_TRY(ar.commit(h));
   oz::Sliced sw, sl;
@@ -226,7 +236,11 @@ extern "C" mgw_status mgw_sigma_moments(mgw_handle* h, const mgw_options* o, int
     oz::place_sliced(wdig, ngroups_t * 128, naux, sw);
     MGW_TRY(oz::slice_grouped(h, nmom, PBt, naux, Wmom, sw));
     MGW_TRY(oz::digit_map(h, &mw, sw, oz::BM));
+    if (mixed)
+      MGW_TRY(oz::global_exponent(h, (long)naux * nmo * nmo, L, reinterpret_cast<unsigned long long*>(st + 1),
+                                  reinterpret_cast<int*>(st + 2)));
   }
+  const int* gexp = tc ? reinterpret_cast<const int*>(st + 2) : nullptr;
 
   for (int sector = 0; sector < 2; ++sector) {
     const int xbeg = sector == 0 ? 0 : nocc, xend = sector == 0 ? nocc : nmo;
@@ -246,11 +260,20 @@ extern "C" mgw_status mgw_sigma_moments(mgw_handle* h, const mgw_options* o, int
       const int nx = std::min(xc, xend - x0);
       const long ncol = (long)nx * nmo;
       if (tc) {
-        oz::place_sliced(ldig, ncol, naux, sl);
-        MGW_TRY(oz::slice_cols(h, ncol, naux, L + (long)x0 * nmo, (long)nmo * nmo, sl));
+        oz::place_sliced(ldig, ncol, naux, sl, lns);
+        if (mixed)
+          MGW_TRY(oz::slice_gather_grid(h, ncol, naux, L + (long)x0 * nmo,
+                                        oz::Gather{ncol + 1, 0, 1, naux + 1L, 0, (long)nmo * nmo}, gexp, sl));
+        else
+          MGW_TRY(oz::slice_cols(h, ncol, naux, L + (long)x0 * nmo, (long)nmo * nmo, sl));
         CUtensorMap ml;
         MGW_TRY(oz::digit_map(h, &ml, sl, oz::BN));
         auto launch_y = [&](auto epi) {
+          if (mixed)
+            return oz::ozaki_launch<oz::kSlices, oz::kGridSlices>(h, mw, ml, sw.exps, sl.exps,
+                                                                  (int)(ngroups_t * 128), (int)ncol, naux,
+                                                                  oz::ARowsPlain{}, epi, dstatus,
+                                                                  "sigma_y_binomial_tc");
           return oz::ozaki_launch(h, mw, ml, sw.exps, sl.exps, (int)(ngroups_t * 128), (int)ncol, naux,
                                   oz::ARowsPlain{}, epi, dstatus, "sigma_y_binomial_tc");
         };
@@ -271,10 +294,13 @@ extern "C" mgw_status mgw_sigma_moments(mgw_handle* h, const mgw_options* o, int
         // on the tensor cores: A rows p, B rows (n, q), both with K = (x_local, P)
         const long K2 = (long)nx * naux;
         oz::Sliced sa2, sz2;
-        oz::place_sliced(adig, nmo, K2, sa2);
+        oz::place_sliced(adig, nmo, K2, sa2, lns);
         oz::place_sliced(zdig, (long)nmom * nmo, K2, sz2);
-        MGW_TRY(oz::slice_gather(h, nmo, K2, L + (long)x0 * nmo,
-                                 oz::Gather{nmo + 1L, 0, 1, naux, nmo, (long)nmo * nmo}, sa2));
+        const oz::Gather ga2{nmo + 1L, 0, 1, naux, nmo, (long)nmo * nmo};
+        if (mixed)
+          MGW_TRY(oz::slice_gather_grid(h, nmo, K2, L + (long)x0 * nmo, ga2, gexp, sa2));
+        else
+          MGW_TRY(oz::slice_gather(h, nmo, K2, L + (long)x0 * nmo, ga2, sa2));
         MGW_TRY(oz::slice_gather(h, (long)nmom * nmo, K2, Z, oz::Gather{nmo, (long)naux * ncol, 1, naux, nmo, ncol},
                                  sz2));
         CUtensorMap ma2, mz2;
@@ -284,14 +310,19 @@ extern "C" mgw_status mgw_sigma_moments(mgw_handle* h, const mgw_options* o, int
         // buffer per split, summed into Sigma by k_reduce_splits)
         const int ns2 = std::min(nsplit_tc, gemm2_splits(nmo, nmom, K2, sms));
         const int nz = oz::split_count(K2, ns2);
+        auto launch_g2 = [&](const oz::FSigmaN& f, int nsp) {
+          const oz::EpiElem<oz::FSigmaN> epi{f};
+          if (mixed)
+            return oz::ozaki_launch<oz::kGridSlices, oz::kSlices>(h, ma2, mz2, sa2.exps, sz2.exps, nmo, nmom * nmo,
+                                                                  (int)K2, oz::ARowsPlain{}, epi, dstatus,
+                                                                  "sigma_gemm2_tc", nsp);
+          return oz::ozaki_launch(h, ma2, mz2, sa2.exps, sz2.exps, nmo, nmom * nmo, (int)K2, oz::ARowsPlain{}, epi,
+                                  dstatus, "sigma_gemm2_tc", nsp);
+        };
         if (nz == 1) {
-          MGW_TRY((oz::ozaki_launch(h, ma2, mz2, sa2.exps, sz2.exps, nmo, nmom * nmo, (int)K2, oz::ARowsPlain{},
-                                    oz::EpiElem<oz::FSigmaN>{oz::FSigmaN{sig, nmo, first ? 0.0 : 1.0, 0}},
-                                    dstatus, "sigma_gemm2_tc")));
+          MGW_TRY(launch_g2(oz::FSigmaN{sig, nmo, first ? 0.0 : 1.0, 0}, 1));
         } else {
-          MGW_TRY((oz::ozaki_launch(h, ma2, mz2, sa2.exps, sz2.exps, nmo, nmom * nmo, (int)K2, oz::ARowsPlain{},
-                                    oz::EpiElem<oz::FSigmaN>{oz::FSigmaN{part, nmo, 0.0, (long)nmom * n2}},
-                                    dstatus, "sigma_gemm2_tc", ns2)));
+          MGW_TRY(launch_g2(oz::FSigmaN{part, nmo, 0.0, (long)nmom * n2}, ns2));
           const long cnt = (long)nmom * n2;
           k_reduce_splits<<<(unsigned)std::min<long>((cnt + 255) / 256, 152L * 16), 256, 0, h->stream>>>(
               cnt, nz, part, sig, first ? 0 : 1);

@@ -15,7 +15,7 @@ import torch
 from . import build as _build
 
 MGW_TDA, MGW_RPA = 0, 1
-MGW_FP64, MGW_BF16X3, MGW_FP64_TC = 0, 1, 2
+MGW_FP64, MGW_BF16X3, MGW_FP64_TC, MGW_MIXED = 0, 1, 2, 3
 
 _STATUS = {
     0: "MGW_OK", -1: "MGW_ERR_ARG", -2: "MGW_ERR_CUDA", -3: "MGW_ERR_NOMEM", -4: "MGW_ERR_NOT_PD",

@@ -1,5 +1,5 @@
-"""Parity at the benchmark's full size (nocc 60, nvir 340, naux 1600,
-nmom_max 7, TDA, FP64), in the launch configuration bench.py times.
+"""Parity at the 400-orbital size (nocc 60, nvir 340, naux 1600, nmom_max 7,
+TDA) on every precision, in the launch configuration bench.py uses.
 
 The oracle cannot afford every output here, so it computes samples it can
 reach directly: rows of W(t) (row P of eta~(n) = V A^n depends on row P of V
@@ -23,7 +23,7 @@ def rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
-@pytest.fixture(scope="module", params=["fp64", "fp64_tc"])
+@pytest.fixture(scope="module", params=["fp64", "fp64_tc", "mixed"])
 def run(request):
     from paper_2504_17439_gb300 import build, driver, mgw
 
@@ -31,28 +31,39 @@ def run(request):
     shape, seed = mgw_inputs.workload("g0w0-nmo400-naux1600")
     eps, L = mgw_inputs.system(shape, seed)
     h = mgw.Handle(0)
-    o = mgw.options(precision=mgw.MGW_FP64 if request.param == "fp64" else mgw.MGW_FP64_TC)
+    o = mgw.options(precision={"fp64": mgw.MGW_FP64, "fp64_tc": mgw.MGW_FP64_TC,
+                               "mixed": mgw.MGW_MIXED}[request.param])
     r = driver.g0w0(h, torch.from_numpy(eps).cuda(), torch.from_numpy(L).cuda(), shape.nocc, shape.nmom_max, opts=o)
     out = {k: (v.cpu().numpy() if isinstance(v, torch.Tensor) else v) for k, v in r.items()
            if k not in ("hole", "part")}
     out["hole"] = tuple(x.cpu().numpy() if isinstance(x, torch.Tensor) else x for x in r["hole"])
     out["part"] = tuple(x.cpu().numpy() if isinstance(x, torch.Tensor) else x for x in r["part"])
+    out["precision"] = request.param
     h.close()
     return shape, eps, L, out
 
 
+def contracted(out, L, nocc):
+    """(V, L) as the run's precision contracts them: on their 16-bit grids
+    under MGW_MIXED, as given otherwise."""
+    V = orc.particle_hole_block(L, nocc)
+    if out["precision"] == "mixed":
+        return orc.fixed_point_grid(V), orc.fixed_point_grid(L)
+    return V, L
+
+
 @pytest.fixture(scope="module")
 def oracle_W(run):
-    shape, eps, L, _ = run
+    shape, eps, L, out = run
     D = orc.energy_differences(eps, shape.nocc)
-    return orc.tda_response_moments(orc.particle_hole_block(L, shape.nocc), D, shape.nmom)
+    return orc.tda_response_moments(contracted(out, L, shape.nocc)[0], D, shape.nmom)
 
 
 def test_response_rows_sampled(run):
     shape, eps, L, out = run
     rows = [0, 1, 777, 1598, 1599]
     D = orc.energy_differences(eps, shape.nocc)
-    Wr = orc.tda_response_moments(orc.particle_hole_block(L, shape.nocc), D, shape.nmom, rows=rows)
+    Wr = orc.tda_response_moments(contracted(out, L, shape.nocc)[0], D, shape.nmom, rows=rows)
     for n in range(shape.nmom):
         assert rel(out["W"][n][rows], Wr[n]) < TOL, (n, rel(out["W"][n][rows], Wr[n]))
 
@@ -60,7 +71,7 @@ def test_response_rows_sampled(run):
 def test_sigma_rows_sampled(run, oracle_W):
     shape, eps, L, out = run
     rows = [0, 59, 60, 217, 399]  # first/last occupied, first virtual, middle, last
-    rh, rp = orc.sigma_moments(eps, shape.nocc, L, oracle_W, rows=rows)
+    rh, rp = orc.sigma_moments(eps, shape.nocc, contracted(out, L, shape.nocc)[1], oracle_W, rows=rows)
     for n in range(shape.nmom):
         assert rel(out["sigma_hole"][n][rows], rh[n]) < TOL, ("hole", n)
         assert rel(out["sigma_part"][n][rows], rp[n]) < TOL, ("particle", n)
@@ -99,3 +110,23 @@ def test_qp_sum_rules(run):
     assert abs(out["nelec"] - 2 * shape.nocc) < 0.1
     assert out["eps_qp"][shape.nocc - 1] < out["mu"] < out["eps_qp"][shape.nocc]
     assert np.all(np.diff(out["E"]) >= 0)
+
+
+@pytest.fixture(scope="module")
+def oracle_full():
+    shape, seed = mgw_inputs.workload("g0w0-nmo400-naux1600")
+    eps, L = mgw_inputs.system(shape, seed)
+    return orc.g0w0(eps, L, shape.nocc, shape.nmom_max)
+
+
+def test_qp_energies_against_the_full_oracle(run, oracle_full):
+    """The whole oracle chain at this size (about a minute on the host, run
+    once per module).  At N = 7 the moment-to-block step amplifies rounding
+    by about 1e2 per block, so two FP64 computations of the same QP energies
+    already differ by a few 0.1 meV here; every tensor-core path is held to
+    the mixed path's bar, 1 meV, against the unrounded FP64 oracle."""
+    shape, eps, L, out = run
+    if out["precision"] == "fp64":
+        pytest.skip("the FP64-unit path is held to the oracle on sampled rows and at the 24-orbital size")
+    d = np.abs(out["eps_qp"] - oracle_full["eps_qp"]).max()
+    assert d < 3.6749e-5, d
