@@ -427,6 +427,44 @@ mgw_status mgw_qsgw_potential(mgw_handle* h, int nmo, int nblk, int rank_h, int 
                               double delta, double srg_s, double* V);
 
 /*
+ * mgw_qsgw_step -- one outer iteration of quasiparticle self-consistent GW
+ * (Sec. III D).  In the reference orbital basis of h and L:
+ *   1. L' = C^T L C; response moments, Sigma moments and both block-Lanczos
+ *      chains in the orbitals C with energies eps (o->screening, o->precision);
+ *   2. the static potential of mgw_qsgw_potential in those orbitals (reg 0:
+ *      Eqs. 36-37 with delta; reg 1: Eqs. 38-39 with srg_s), carried to the
+ *      reference basis: V = C V' C^T (written to st->V);
+ *   3. Eq. 35 with V held fixed: F = h + J[rho] - K[rho]/2 + V, rho = 2 C_occ
+ *      C_occ^T over the nocc lowest orbitals of F, Pulay DIIS (space
+ *      diis_space, extrapolating once three vectors are held) on the
+ *      commutator F rho - rho F, until max |delta rho| < scf_tol and
+ *      max |F rho - rho F| < 1e3 scf_tol (at most scf_max_iter iterations);
+ *   4. eps, C <- eigh(F of the final density); de = max |eps_new - eps_old|.
+ * Start from C = I, eps = the reference energies for a canonical
+ * Hartree-Fock reference (h from mgw_hf_core); repeat until de is below the
+ * caller's tolerance.  The eigensolves are cuSOLVER syevd (they synchronise).
+ */
+typedef struct {
+  int nocc, nvir, naux, nmom_max; /* sizes; nmom_max <= 11 */
+  const double* h;        /* [nmo][nmo]        in   core Hamiltonian, reference basis */
+  const double* L;        /* [naux][nmo][nmo]  in   DF tensor, reference basis */
+  double* C;              /* [nmo][nmo]        in/out orbitals (columns) */
+  double* eps;            /* [nmo]             in/out orbital energies (ascending on output) */
+  double* F;              /* [nmo][nmo]        out  the field of Eq. 35 at the end of the step */
+  double* V;              /* [nmo][nmo]        out  the static potential in the reference basis */
+  int reg;                /* host in: 0 = delta-broadened (Eqs. 36-37), 1 = SRG (Eqs. 38-39) */
+  double delta, srg_s;    /* host in: broadening (reg 0, > 0) and flow parameter (reg 1, >= 0) */
+  int diis_space;         /* host in: DIIS vectors kept (1..32) */
+  int scf_max_iter;       /* host in: cap of the Eq. 35 iterations */
+  double scf_tol;         /* host in: density tolerance of the Eq. 35 loop */
+  double de;              /* host out */
+  int scf_iters;          /* host out */
+  int scf_converged;      /* host out: 1 if the Eq. 35 loop met its tolerance */
+} mgw_qsgw_state;
+
+mgw_status mgw_qsgw_step(mgw_handle* h, const mgw_options* o, mgw_qsgw_state* st);
+
+/*
  * Warm-start network (not in the paper): three dense layers with SiLU,
  *   z1 = W1 x + b1, a1 = silu(z1); z2 = W2 a1 + b2, a2 = silu(z2); y = W3 a2 + b3.
  * params: FP32 master vector [W1 | b1 | W2 | b2 | W3 | b3] (W row-major
@@ -458,8 +496,9 @@ mgw_status mgw_mlp_adam(mgw_handle* h, long n, float* params, unsigned short* wb
  * (tcgen05, TMA, TMEM).  Each row of A and B is scaled by a power of two and
  * cut into 7 signed base-256 digits held exactly in BF16; the 28 digit
  * products above 2^-64 of the leading term are integer GEMMs, accumulated
- * exactly in FP32 over K chunks (1024 / (s + u - 1) wide) for the top 10
- * and flushed into 64-bit integers, the rest in FP32 over all of K.  Error:
+ * exactly in FP32 over K chunks (1024 / (s + u - 1) wide) for the 21
+ * products of levels s + u <= 7 and flushed into 64-bit integers, the 7 of
+ * level 8 in FP32 over all of K.  Error:
  * a few units of 2^-53 times sum_k |A_ik| |B_jk|, as an FP64 GEMM.  Not in
  * the paper; it is how the FP64 contractions of the path reach the tensor
  * cores of a GPU whose FP64 units are few.
@@ -472,13 +511,25 @@ mgw_status mgw_gemm_fp64_emu(mgw_handle* h, int M, int N, int K,
  * mgw_gemm_bf16x3 -- C = A B^T on the tensor cores (tcgen05, TMA, TMEM):
  * each FP64 operand is split as x = hi + lo with hi = bf16(x),
  * lo = bf16(x - hi), and C accumulates hi*hi + hi*lo + lo*hi in FP32, then is
- * written as FP64.  The split-precision product of the mixed path; relative
- * error about 1e-5 of |A||B| per element.  Not in the paper (its contractions
- * are FP64); the building block of the precision pattern.
+ * written as FP64.  Relative error about 1e-5 of |A||B| per element, too
+ * coarse for the moment-to-block step (inconsistent moment errors are
+ * amplified about 1e2 per block), so no path uses it; MGW_MIXED rounds the
+ * input tensor instead and keeps every product exact.  Not in the paper.
  *   A [M][K], B [N][K] in (FP64, row-major);  C [M][N] out (FP64)
  */
 mgw_status mgw_gemm_bf16x3(mgw_handle* h, int M, int N, int K,
                            const double* A, const double* B, double* C);
+
+/*
+ * mgw_selftest_bounded_wait -- exercise the error path of the tensor-core
+ * kernels' bounded waits: one CTA waits, with the same time-bounded mbarrier
+ * wait, on a barrier that nothing arrives at.  The wait gives up after
+ * limit_s seconds (0 < limit_s <= 10), raises the status word, and the call
+ * returns MGW_ERR_TIMEOUT with the text in mgw_last_error; the context and
+ * the handle stay usable.  (In the GEMM kernels the same status word also
+ * stops every CTA that starts after it is raised.)  Not in the paper.
+ */
+mgw_status mgw_selftest_bounded_wait(mgw_handle* h, double limit_s);
 
 /*
  * mgw_response_moments_tda_noalloc -- the TDA branch of mgw_response_moments

@@ -23,53 +23,9 @@
 
 namespace mgw {
 
-// the binomial epilogue of sigma.cu, restated for grouped use (same arithmetic)
-struct BinomCoefB {
-  double c[24 * 25 / 2];
-};
-struct EpiBinomialB {
-  static constexpr bool kTile = true;
-  double* Z;
-  const double* eps;
-  int nmom, PB, naux, nmo;
-  long ncol;
-  const BinomCoefB* bc;  // device pointer (hole, particle tables)
-  template <int BM, int BN, int TM, int TN>
-  __device__ void tile(int, long m0, long n0, long, long N, double (&acc)[TM][TN], double* smem, int) const {
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    constexpr int HALF = BN / 2;
-    const long g = m0 / BM;
-    for (int hf = 0; hf < 2; ++hf) {
-      __syncthreads();
-#pragma unroll
-      for (int i = 0; i < TM; ++i)
-#pragma unroll
-        for (int jj = 0; jj < TN / 2; ++jj) {
-          int j = hf * (TN / 2) + jj;
-          smem[(ty + 16 * i) * (HALF + 1) + tx + 16 * j - hf * HALF] = acc[i][j];
-        }
-      __syncthreads();
-      for (int pi = tid; pi < PB * HALF; pi += 256) {
-        int pl = pi / HALF, col = pi % HALF;
-        long P = g * PB + pl, n = n0 + hf * HALF + col;
-        if (P >= naux || n >= N) continue;
-        double e = eps[n / nmo];
-        double y[24], pe[24];
-        pe[0] = 1.0;
-        for (int t = 0; t < nmom; ++t) {
-          y[t] = smem[(t * PB + pl) * (HALF + 1) + col];
-          if (t + 1 < nmom) pe[t + 1] = pe[t] * e;
-        }
-        for (int nn = 0; nn < nmom; ++nn) {
-          const double* cr = bc->c + nn * (nn + 1) / 2;
-          double z = 0.0;
-          for (int t = 0; t <= nn; ++t) z = fma(cr[t] * pe[nn - t], y[t], z);
-          Z[((long)nn * naux + P) * ncol + n] = z;
-        }
-      }
-    }
-  }
-};
+// the Y stage's binomial epilogue (mgw_internal.h) with its coefficient
+// table read through a device pointer (one table per sector for all systems)
+using EpiBinomialB = EpiBinomialT<BinomCoefRef>;
 
 
 // Candidate tile shapes of the grouped FP64 GEMM; static shared memory of
@@ -127,7 +83,7 @@ static void add_launch(Blob& blob, std::vector<Launch>& out, int kind, const std
 
 // the item tables of every launch, in issue order, for tile shapes cfg[kind]
 static std::vector<Launch> build_launches(const std::vector<Sys>& S, const mgw_system* sys, int nsys, int nmom,
-                                          const int cfg[kStKinds], const BinomCoefB* dcoef, int rounds, Blob& blob) {
+                                          const int cfg[kStKinds], const BinomCoef* dcoef, int rounds, Blob& blob) {
   std::vector<Launch> out;
   int bmT, bnT, bmY, bnY;
   cfg_shape(cfg[kStT], bmT, bnT);
@@ -165,7 +121,7 @@ static std::vector<Launch> build_launches(const std::vector<Sys>& S, const mgw_s
         const long ngroups = (q.naux + PB - 1) / PB;
         yi.push_back({ngroups * bmY, ncol, q.naux, AGroupedMoments{q.W, nmom, PB, (int)q.naux, bmY},
                       BRowMajor{sys[s].L + x0 * q.nmo, q.nmo * q.nmo, 0},
-                      EpiBinomialB{q.Z, sys[s].eps + x0, nmom, PB, (int)q.naux, (int)q.nmo, ncol, dcoef + sec}, 0});
+                      EpiBinomialB{q.Z, sys[s].eps + x0, nmom, PB, (int)q.naux, (int)q.nmo, ncol, BinomCoefRef{dcoef + sec}}, 0});
         double* sig = sec == 0 ? sys[s].sig_hole : sys[s].sig_part;
         for (int n = 0; n < nmom; ++n)
           gi.push_back({q.nmo, q.nmo, q.naux * nx, AKMajor2{sys[s].L + x0 * q.nmo, nx, q.nmo * q.nmo, q.nmo, 0},
@@ -422,23 +378,14 @@ extern "C" mgw_status mgw_sigma_moments_batched(mgw_handle* h, const mgw_options
     ar.add(&q.Z, (long)nmom * q.naux * xc * q.nmo);
   }
   double* coef = nullptr;
-  ar.add(&coef, 2 * sizeof(BinomCoefB) / sizeof(double));
+  ar.add(&coef, 2 * sizeof(BinomCoef) / sizeof(double));
   MGW_TRY(ar.commit(h));
-  const BinomCoefB* dcoef = reinterpret_cast<const BinomCoefB*>(coef);
+  const BinomCoef* dcoef = reinterpret_cast<const BinomCoef*>(coef);
 
   // binomial tables 2 C(n,t) s^t for s = -1 (hole) and +1 (particle)
-  BinomCoefB hc[2];
-  for (int sec = 0; sec < 2; ++sec) {
-    const double sgn = sec == 0 ? -1.0 : 1.0;
-    for (int n = 0; n < nmom; ++n) {
-      double c = 1.0, sg = 1.0;
-      for (int t = 0; t <= n; ++t) {
-        hc[sec].c[n * (n + 1) / 2 + t] = 2.0 * c * sg;
-        c = c * (n - t) / (t + 1);
-        sg *= sgn;
-      }
-    }
-  }
+  BinomCoef hc[2];
+  binomial_table(nmom, -1.0, hc[0]);
+  binomial_table(nmom, 1.0, hc[1]);
   MGW_CUDA(h, cudaMemcpyAsync(coef, hc, sizeof hc, cudaMemcpyHostToDevice, h->stream));
 
   // plan keys: the problem's sizes, and its sizes with every pointer

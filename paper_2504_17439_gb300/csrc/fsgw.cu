@@ -102,6 +102,29 @@ static bool diis_coefficients(const std::vector<double>& B, int n, std::vector<d
   return true;
 }
 
+}  // namespace mgw
+
+mgw_status mgw::fock_build(mgw_handle* h, int nmo, int naux, const double* hcore, const double* L,
+                           const double* r, double* out, double* v, double* tmp) {
+  const long n2 = (long)nmo * nmo;
+  // v_P = sum_rs L_Prs rho_rs ; J = sum_P v_P L_P
+  MGW_TRY(gemm_nn(h, naux, 1, n2, 1.0, L, n2, r, 1, 0.0, v, 1));
+  MGW_CUDA(h, cudaMemcpyAsync(out, hcore, sizeof(double) * n2, cudaMemcpyDeviceToDevice, h->stream));
+  MGW_TRY(gemm_nn(h, 1, n2, naux, 1.0, v, naux, L, n2, 1.0, out, n2));
+  // tmp_P = rho L_P (batched); K_pq = sum_{P,r} tmp[P][r][p] L[P][r][q]
+  MGW_TRY((dgemm<64, 64>(h, nmo, nmo, nmo, naux, ARowMajor{r, nmo, 0}, BRowMajor{L, nmo, n2},
+                         EpiStore{tmp, nmo, n2, 1.0, 0.0}, "gemm_nn")));
+  MGW_TRY((dgemm<64, 64>(h, nmo, nmo, (long)naux * nmo, 1, AKMajor2{tmp, nmo, n2, nmo, 0}, BRowMajor{L, nmo, 0},
+                         EpiStore{out, nmo, 0, -0.5, 1.0}, "gemm_tn")));
+  return MGW_OK;
+}
+
+bool mgw::diis_solve(const std::vector<double>& B, int n, std::vector<double>& c) {
+  return diis_coefficients(B, n, c);
+}
+
+namespace mgw {
+
 struct FsgwCtx {
   mgw_handle* h;
   const mgw_options* o;
@@ -119,18 +142,7 @@ struct FsgwCtx {
   }
 
   // F[rho] = h + J - K/2
-  mgw_status fock(const double* r, double* out) {
-    // v_P = sum_rs L_Prs rho_rs ; J = sum_P v_P L_P
-    MGW_TRY(gemm_nn(h, naux, 1, n2, 1.0, L, n2, r, 1, 0.0, v, 1));
-    MGW_CUDA(h, cudaMemcpyAsync(out, hcore, sizeof(double) * n2, cudaMemcpyDeviceToDevice, h->stream));
-    MGW_TRY(gemm_nn(h, 1, n2, naux, 1.0, v, naux, L, n2, 1.0, out, n2));
-    // tmp_P = rho L_P (batched); K_pq = sum_{P,r} tmp[P][r][p] L[P][r][q]
-    MGW_TRY((dgemm<64, 64>(h, nmo, nmo, nmo, naux, ARowMajor{r, nmo, 0}, BRowMajor{L, nmo, n2},
-                           EpiStore{tmp, nmo, n2, 1.0, 0.0}, "gemm_nn")));
-    MGW_TRY((dgemm<64, 64>(h, nmo, nmo, (long)naux * nmo, 1, AKMajor2{tmp, nmo, n2, nmo, 0},
-                           BRowMajor{L, nmo, 0}, EpiStore{out, nmo, 0, -0.5, 1.0}, "gemm_tn")));
-    return MGW_OK;
-  }
+  mgw_status fock(const double* r, double* out) { return fock_build(h, nmo, naux, hcore, L, r, out, v, tmp); }
 
   mgw_status nerr(const double* F, double zeta, double* err) {
     double ne = 0, mu = 0;

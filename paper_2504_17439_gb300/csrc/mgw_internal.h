@@ -408,5 +408,91 @@ mgw_status energy_differences(mgw_handle* h, int nocc, int nvir, const double* e
 mgw_status scale_columns(mgw_handle* h, long rows, long cols, const double* src, const double* d,
                          double* dst);  // dst[r][c] = src[r][c] * d[c]
 mgw_status add_identity(mgw_handle* h, int n, double* a, double s);  // a += s * I
+// Fock build of a restricted closed-shell reference, F[rho] = hcore + J[rho]
+// - K[rho]/2 with J_pq = sum_P L_Ppq sum_rs L_Prs rho_rs and K_pq =
+// sum_P sum_rs L_Ppr rho_rs L_Psq (rho spin-summed); scratch v [naux],
+// tmp [naux][nmo][nmo]
+mgw_status fock_build(mgw_handle* h, int nmo, int naux, const double* hcore, const double* L, const double* rho,
+                      double* out, double* v, double* tmp);
+// Pulay DIIS coefficients on the host: minimise |sum c_i e_i| subject to
+// sum c_i = 1 from the Gram matrix B [n][n] of the errors; false if singular
+bool diis_solve(const std::vector<double>& B, int n, std::vector<double>& c);
+
+
+// ---- Y-stage tile epilogue of the FP64 Sigma build (Eqs. 6-7): rows of the
+// tile are (t, pl) with t = r / PB, pl = r % PB; columns (x_local, q) of the
+// chunk.  The epilogue stages the tile in shared memory, half the columns at
+// a time, and writes only
+//   Z(n)[P][(x,q)] = sum_{t<=n} c(n,t) eps_x^(n-t) Y(t)[P][(x,q)],
+// c(n,t) = 2 C(n,t) s^t from a table (s = -1 hole, +1 particle), so Y never
+// reaches HBM.  Coef gives the table: held by value (one launch, one sector)
+// or through a device pointer (grouped launches over many systems).
+constexpr int kMaxBinomMom = 24;
+struct BinomCoef {
+  double c[kMaxBinomMom * (kMaxBinomMom + 1) / 2];  // c(n,t) at n(n+1)/2 + t
+  __device__ const double* row(int n) const { return c + n * (n + 1) / 2; }
+};
+struct BinomCoefRef {
+  const BinomCoef* p;
+  __device__ const double* row(int n) const { return p->row(n); }
+};
+template <class Coef>
+struct EpiBinomialT {
+  static constexpr bool kTile = true;
+  double* Z;           // [nmom][naux][ncol]
+  const double* eps;   // eps_x of the chunk's first x at eps[0]
+  int nmom, PB, naux, nmo;
+  long ncol;           // xc * nmo
+  Coef bc;
+
+  template <int BM, int BN, int TM, int TN>
+  __device__ void tile(int, long m0, long n0, long, long N, double (&acc)[TM][TN], double* smem, int) const {
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    constexpr int HALF = BN / 2;  // stage half the columns at a time
+    static_assert((TN % 2) == 0, "TN must be even");
+    const long g = m0 / BM;       // tile == one group of PB aux rows
+    for (int hf = 0; hf < 2; ++hf) {
+      __syncthreads();
+      // acc columns tx + 16 j with j in [hf*TN/2, (hf+1)*TN/2) -> smem [BM][HALF+1]
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int jj = 0; jj < TN / 2; ++jj) {
+          const int j = hf * (TN / 2) + jj;
+          smem[(ty + 16 * i) * (HALF + 1) + tx + 16 * j - hf * HALF] = acc[i][j];
+        }
+      __syncthreads();
+      for (int pi = tid; pi < PB * HALF; pi += 256) {
+        const int pl = pi / HALF, col = pi % HALF;
+        const long P = g * PB + pl, n = n0 + hf * HALF + col;
+        if (P >= naux || n >= N) continue;
+        const double e = eps[n / nmo];
+        double y[kMaxBinomMom], pe[kMaxBinomMom];
+        pe[0] = 1.0;
+        for (int t = 0; t < nmom; ++t) {
+          y[t] = smem[(t * PB + pl) * (HALF + 1) + col];
+          if (t + 1 < nmom) pe[t + 1] = pe[t] * e;
+        }
+        for (int nn = 0; nn < nmom; ++nn) {
+          const double* cr = bc.row(nn);
+          double z = 0.0;
+          for (int t = 0; t <= nn; ++t) z = fma(cr[t] * pe[nn - t], y[t], z);
+          Z[((long)nn * naux + P) * ncol + n] = z;
+        }
+      }
+    }
+  }
+};
+// the table c(n,t) = 2 C(n,t) s^t for one sector
+inline void binomial_table(int nmom, double s, BinomCoef& bc) {
+  for (int n = 0; n < nmom; ++n) {
+    double c = 1.0, sg = 1.0;
+    for (int t = 0; t <= n; ++t) {
+      bc.c[n * (n + 1) / 2 + t] = 2.0 * c * sg;
+      c = c * (n - t) / (t + 1);
+      sg *= s;
+    }
+  }
+}
 
 }  // namespace mgw

@@ -362,6 +362,39 @@ void place_sliced(double* mem, long rows, long K, Sliced& s, int ns) {
 }  // namespace oz
 }  // namespace mgw
 
+namespace mgw {
+namespace oz {
+// One CTA waits, with the pipeline's bounded wait, on an mbarrier that
+// nothing ever arrives at; the wait must give up after limit_ns and raise
+// the status word (the error path every tensor-core kernel takes).
+__global__ void k_bounded_wait_selftest(unsigned long long limit_ns, int* status) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_barrier_init();
+  }
+  __syncthreads();
+  if (!tc::mbar_wait(&bar, 0, limit_ns) && threadIdx.x == 0) atomicCAS(status, tc::kOk, tc::kTimeoutFull);
+}
+}  // namespace oz
+}  // namespace mgw
+
+extern "C" mgw_status mgw_selftest_bounded_wait(mgw_handle* h, double limit_s) {
+  if (!h) return MGW_ERR_ARG;
+  if (!(limit_s > 0.0 && limit_s <= 10.0))
+    return fail(h, MGW_ERR_ARG, "mgw_selftest_bounded_wait: limit %g s outside (0, 10]", limit_s);
+  MGW_CUDA(h, cudaSetDevice(h->device));
+  Arena ar;
+  double* st;
+  ar.add(&st, 1);
+  MGW_TRY(ar.commit(h));
+  int* dstatus = reinterpret_cast<int*>(st);
+  MGW_CUDA(h, cudaMemsetAsync(dstatus, 0, sizeof(int), h->stream));
+  oz::k_bounded_wait_selftest<<<1, 32, 0, h->stream>>>((unsigned long long)(limit_s * 1e9), dstatus);
+  MGW_TRY(check_launch(h, "bounded_wait_selftest"));
+  return tc::check_tc_status(h, dstatus, "mgw_selftest_bounded_wait");
+}
+
 extern "C" mgw_status mgw_gemm_fp64_emu(mgw_handle* h, int M, int N, int K, const double* A, const double* B,
                                         double* C) {
   if (!h) return MGW_ERR_ARG;

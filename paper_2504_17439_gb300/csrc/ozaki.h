@@ -231,7 +231,8 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
   uint64_t* empty = full + kGroups;
   uint64_t* accf = empty + kGroups;  // [2] accumulator b ready for the epilogue
   uint64_t* acce = accf + 2;         // [2] accumulator b drained by the epilogue
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
+  uint64_t* drain = acce + 2;        // MMAs issued before an abort have completed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   int* col_exp = reinterpret_cast<int*>(smem + kStages * kStageBytes + kBarBytes);  // [BN]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -258,6 +259,10 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
   // tiles the epilogue does not need (the lower triangle of a symmetric
   // result) end here, before any barrier, TMEM or shared-memory set-up
   if (epi.skip_tile(m0, n0, M, N)) return;
+  // a wait of an earlier CTA (or launch on this status word) gave up: the
+  // result is void, so do no set-up and no work (a failing launch then ends
+  // within one wave instead of every CTA waiting out its own limits)
+  if (*reinterpret_cast<volatile int*>(status) != kOk) return;
   // split z = blockIdx.y covers k in [k0, k0 + ksplit); its partial result
   // goes where the epilogue puts split z
   const int k0 = (int)blockIdx.y * ksplit;
@@ -272,6 +277,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
       mbar_init(&accf[b], 1);
       mbar_init(&acce[b], 8);
     }
+    mbar_init(drain, 1);
     fence_barrier_init();
   }
   if (warp == kMmaWarp) {
@@ -318,19 +324,24 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
       return true;
     });
     // before leaving, this producer's groups among the last kGroups have landed
+    // (no copy may still write into this CTA's shared memory once it exits)
     const int ng = (it + kGroup - 1) / kGroup;
     for (int g = (ng > kGroups ? ng - kGroups : 0); g < ng; ++g)
-      if ((g % kGroups) % kProducers == warp) mbar_wait(&full[g % kGroups], (g / kGroups) & 1, kWaitNs);
+      if ((g % kGroups) % kProducers == warp && !mbar_wait(&full[g % kGroups], (g / kGroups) & 1, kWaitNs) &&
+          lane == 0)
+        atomicCAS(status, kOk, kTimeoutDrain);
   } else if (warp == kMmaWarp) {
     // the whole warp walks the schedule and waits; one elected lane issues
     const uint32_t idesc = idesc_bf16_f32(BM, BN);
     const int total = sched.items();
     int it = 0;
+    bool aborted = false;
     sched.run([&](int phase, bool, int, int, int, int, bool first, bool last) {
       const int b = phase & 1, use = phase >> 1;
       if (first) {
         if (!mbar_wait(&acce[b], (use & 1) ^ 1, kWaitNs)) {
           if (lane == 0) atomicCAS(status, kOk, kTimeoutEpi);
+          aborted = true;
           return false;
         }
         tc_fence_after();
@@ -340,6 +351,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
       if (it % kGroup == 0) {
         if (!mbar_wait(&full[gs], (g / kGroups) & 1, kWaitNs)) {
           if (lane == 0) atomicCAS(status, kOk, kTimeoutFull);
+          aborted = true;
           return false;
         }
         tc_fence_after();
@@ -359,6 +371,13 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
       ++it;
       return true;
     });
+    // after an abort the MMAs already issued must finish before TMEM is freed
+    if (aborted && it > 0) {
+      if (elect_one()) mma_commit(drain);
+      __syncwarp();
+      if (!mbar_wait(drain, 0, kWaitNs) && lane == 0) atomicCAS(status, kOk, kTimeoutDrain);
+      tc_fence_after();
+    }
   } else if (warp >= kEpiWarp0) {
     // ---------------- epilogue warps 4..11
     const int quad = warp & 3, half = (warp - kEpiWarp0) >> 2;

@@ -32,11 +32,7 @@
 
 namespace mgw {
 
-constexpr int kMaxMom = 24;
-
-struct BinomCoef {
-  double c[kMaxMom * (kMaxMom + 1) / 2];  // 2 C(n,t) s^t, row n at n(n+1)/2
-};
+constexpr int kMaxMom = kMaxBinomMom;
 
 // Binomial epilogue of the tensor-core Y stage.  Each of the 256 epilogue
 // threads holds 48 FP64 results of one tile row (t, pl); they are staged in
@@ -92,60 +88,6 @@ struct EpiBinomialTC {
     }
   }
   __device__ void abort() const { tc::named_bar(1, 256); }
-};
-
-// Tile epilogue of the Y stage: rows of the tile are (t, pl) with
-// t = r / PB, pl = r % PB; columns are (x_local, q) of the chunk.
-struct EpiBinomial {
-  static constexpr bool kTile = true;
-  double* Z;           // [nmom][naux][ncol]
-  const double* eps;   // eps_x of the chunk's first x at eps[0]
-  int nmom, PB, naux, nmo;
-  long ncol;           // xc * nmo
-  BinomCoef bc;
-
-  template <int BM, int BN, int TM, int TN>
-  __device__ void tile(int, long m0, long n0, long, long N, double (&acc)[TM][TN], double* smem,
-                       int smem_len) const {
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    constexpr int HALF = BN / 2;  // stage half the columns at a time
-    static_assert((TN % 2) == 0, "TN must be even");
-    const long g = m0 / BM;        // tile == one group of PB aux rows
-    (void)smem_len;
-    for (int hf = 0; hf < 2; ++hf) {
-      __syncthreads();
-      // acc columns tx + 16 j with j in [hf*TN/2, (hf+1)*TN/2) -> smem [BM][HALF+1]
-#pragma unroll
-      for (int i = 0; i < TM; ++i)
-#pragma unroll
-        for (int jj = 0; jj < TN / 2; ++jj) {
-          int j = hf * (TN / 2) + jj;
-          int col = tx + 16 * j - hf * HALF;
-          smem[(ty + 16 * i) * (HALF + 1) + col] = acc[i][j];
-        }
-      __syncthreads();
-      const int pairs = PB * HALF;
-      for (int pi = tid; pi < pairs; pi += 256) {
-        int pl = pi / HALF, col = pi % HALF;
-        long P = g * PB + pl;
-        long n = n0 + hf * HALF + col;
-        if (P >= naux || n >= N) continue;
-        double e = eps[n / nmo];
-        double y[kMaxMom], pe[kMaxMom];
-        pe[0] = 1.0;
-        for (int t = 0; t < nmom; ++t) {
-          y[t] = smem[(t * PB + pl) * (HALF + 1) + col];
-          if (t + 1 < nmom) pe[t + 1] = pe[t] * e;
-        }
-        for (int nn = 0; nn < nmom; ++nn) {
-          const double* cr = bc.c + nn * (nn + 1) / 2;
-          double z = 0.0;
-          for (int t = 0; t <= nn; ++t) z = fma(cr[t] * pe[nn - t], y[t], z);
-          Z[((long)nn * naux + P) * ncol + n] = z;
-        }
-      }
-    }
-  }
 };
 
 // K splits of the tensor-core GEMM2 (rows p, columns (n, q), K = nx naux),
@@ -247,14 +189,7 @@ extern "C" mgw_status mgw_sigma_moments(mgw_handle* h, const mgw_options* o, int
     const double sgn = sector == 0 ? -1.0 : 1.0;
     double* sig = sector == 0 ? sig_hole : sig_part;
     BinomCoef bc;
-    for (int n = 0; n < nmom; ++n) {
-      double c = 1.0, s = 1.0;
-      for (int t = 0; t <= n; ++t) {
-        bc.c[n * (n + 1) / 2 + t] = 2.0 * c * s;
-        c = c * (n - t) / (t + 1);
-        s *= sgn;
-      }
-    }
+    binomial_table(nmom, sgn, bc);
     bool first = true;
     for (int x0 = xbeg; x0 < xend; x0 += xc) {
       const int nx = std::min(xc, xend - x0);
@@ -284,7 +219,7 @@ extern "C" mgw_status mgw_sigma_moments(mgw_handle* h, const mgw_options* o, int
         else
           MGW_TRY(launch_y(EpiBinomialTC<kMaxMom>{Z, eps_G + x0, nmom, PBt, naux, nmo, ncol, sgn}));
       } else {
-        EpiBinomial epi{Z, eps_G + x0, nmom, PB, naux, nmo, ncol, bc};
+        EpiBinomialT<BinomCoef> epi{Z, eps_G + x0, nmom, PB, naux, nmo, ncol, bc};
         AGroupedMoments A{Wmom, nmom, PB, naux, BM};
         BRowMajor B{L + (long)x0 * nmo, (long)nmo * nmo, 0};
         MGW_TRY((dgemm<BM, BN>(h, ngroups * BM, ncol, naux, 1, A, B, epi, "sigma_y_binomial")));

@@ -13,7 +13,7 @@ namespace mgw {
 namespace tc {
 
 // error flag codes written to the kernel's status word
-enum : int { kOk = 0, kTimeoutFull = 1, kTimeoutEmpty = 2, kTimeoutAccum = 3, kTimeoutEpi = 4 };
+enum : int { kOk = 0, kTimeoutFull = 1, kTimeoutEmpty = 2, kTimeoutAccum = 3, kTimeoutEpi = 4, kTimeoutDrain = 5 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));

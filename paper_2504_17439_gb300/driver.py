@@ -121,6 +121,38 @@ def fsgw(h: mgw.Handle, hcore: torch.Tensor, L: torch.Tensor, eps: torch.Tensor,
     return dict(eps_qp=eps_qp, F=F, zeta=st.zeta, mu=st.mu, converged=False, history=hist)
 
 
+def qsgw(h: mgw.Handle, hcore: torch.Tensor, L: torch.Tensor, eps: torch.Tensor, nocc: int, nmom_max: int,
+         reg: str = "srg", delta: float = 1e-3, srg_s: float = 100.0, screening: int = mgw.MGW_TDA,
+         opts: mgw.Options | None = None, conv: float = 1e-8, max_outer: int = 60, diis_space: int = 8,
+         scf_tol: float = 1e-10, scf_max_iter: int = 200) -> dict:
+    """Quasiparticle self-consistent GW (Sec. III D): mgw_qsgw_step until the
+    orbital energies change by less than `conv` between outer steps.  hcore
+    and L in the reference basis, eps the reference energies (a canonical
+    Hartree-Fock reference: C starts as the identity)."""
+    o = opts if opts is not None else mgw.options()
+    o.screening = screening
+    naux, nmo = L.shape[0], L.shape[1]
+    dev = L.device
+    for name, t in (("hcore", hcore), ("L", L), ("eps", eps)):
+        if not t.is_cuda or t.dtype != torch.float64:
+            raise ValueError(f"{name} must be a float64 CUDA tensor")
+    hcore, L = hcore.contiguous(), L.contiguous()
+    C = torch.eye(nmo, dtype=torch.float64, device=dev)
+    e = eps.clone().contiguous()
+    F = torch.empty((nmo, nmo), dtype=torch.float64, device=dev)
+    V = torch.empty_like(F)
+    st = mgw.QsgwState(nocc, nmo - nocc, naux, nmom_max, hcore.data_ptr(), L.data_ptr(), C.data_ptr(), e.data_ptr(),
+                       F.data_ptr(), V.data_ptr(), {"eta": 0, "srg": 1}[reg], delta, srg_s, diis_space, scf_max_iter,
+                       scf_tol)
+    hist = []
+    for outer in range(max_outer):
+        h.mgw_qsgw_step(o, st)
+        hist.append(dict(outer=outer, de=st.de, scf_iter=st.scf_iters, scf_converged=bool(st.scf_converged)))
+        if st.de < conv:
+            return dict(eps=e, C=C, F=F, V=V, converged=True, history=hist)
+    return dict(eps=e, C=C, F=F, V=V, converged=False, history=hist)
+
+
 class WarmStart:
     """The learned warm start of the fsGW zeta search: a 3-layer SiLU network
     (BF16 weights, FP32 accumulation) trained on (features, zeta - zeta_prev)

@@ -45,6 +45,17 @@ class Options(ctypes.Structure):
     ]
 
 
+class QsgwState(ctypes.Structure):
+    _fields_ = [
+        ("nocc", ctypes.c_int), ("nvir", ctypes.c_int), ("naux", ctypes.c_int), ("nmom_max", ctypes.c_int),
+        ("h", ctypes.c_void_p), ("L", ctypes.c_void_p), ("C", ctypes.c_void_p), ("eps", ctypes.c_void_p),
+        ("F", ctypes.c_void_p), ("V", ctypes.c_void_p), ("reg", ctypes.c_int), ("delta", ctypes.c_double),
+        ("srg_s", ctypes.c_double), ("diis_space", ctypes.c_int), ("scf_max_iter", ctypes.c_int),
+        ("scf_tol", ctypes.c_double), ("de", ctypes.c_double), ("scf_iters", ctypes.c_int),
+        ("scf_converged", ctypes.c_int),
+    ]
+
+
 class FsgwState(ctypes.Structure):
     _fields_ = [
         ("nocc", ctypes.c_int), ("nvir", ctypes.c_int), ("naux", ctypes.c_int), ("nmom_max", ctypes.c_int),
@@ -90,6 +101,7 @@ _SIGS = {
     "mgw_extract_ov": [_I, _I, _I, _P, _P],
     "mgw_gemm_bf16x3": [_I, _I, _I, _P, _P, _P],
     "mgw_gemm_fp64_emu": [_I, _I, _I, _P, _P, _P],
+    "mgw_selftest_bounded_wait": [_D],
     "mgw_response_moments": [_P, _I, _I, _I, _I, _P, _P, _P],
     "mgw_sigma_moments": [_P, _I, _I, _I, _I, _P, _P, _P, _P, _P],
     "mgw_block_lanczos": [_P, _I, _I, _P, _P, _P, _P, ctypes.POINTER(_I)],
@@ -142,6 +154,8 @@ def load(path: str | None = None):
     lib.mgw_sigma_moments_batched.restype = _I
     lib.mgw_fsgw_step.argtypes = [_P, _P, ctypes.POINTER(FsgwState)]
     lib.mgw_fsgw_step.restype = _I
+    lib.mgw_qsgw_step.argtypes = [_P, _P, ctypes.POINTER(QsgwState)]
+    lib.mgw_qsgw_step.restype = _I
     lib.mgw_hf_core.argtypes = [_P, _I, _I, _I, _P, _P, _P]
     lib.mgw_hf_core.restype = _I
     lib.mgw_g0w0_batched.argtypes = [_P, _P, _I, _I, ctypes.POINTER(G0w0System)]
@@ -372,6 +386,10 @@ class Handle:
                                            self._fptr(wbf16, "wbf16"), self._fptr(grad, "grad"),
                                            self._fptr(m, "m"), self._fptr(v, "v"), step, float(lr)))
 
+    def mgw_qsgw_step(self, opts: Options, st: QsgwState):
+        self._check(self._lib.mgw_qsgw_step(self._h, ctypes.byref(opts), ctypes.byref(st)))
+        return st
+
     def mgw_fsgw_step(self, opts: Options, st: FsgwState):
         self._check(self._lib.mgw_fsgw_step(self._h, ctypes.byref(opts), ctypes.byref(st)))
         return st
@@ -384,6 +402,10 @@ class Handle:
         self._check(self._lib.mgw_gemm_fp64_emu(self._h, M, N, K, _ptr(A, (M, K), "A"), _ptr(B, (N, K), "B"),
                                                 _ptr(C, (M, N), "C")))
         return C
+
+    def mgw_selftest_bounded_wait(self, limit_s):
+        """A bounded wait that nothing satisfies: raises MgwError(MGW_ERR_TIMEOUT)."""
+        self._check(self._lib.mgw_selftest_bounded_wait(self._h, float(limit_s)))
 
     def mgw_gemm_bf16x3(self, A, B, C=None):
         """C = A B^T on the tensor cores with BF16 hi/lo operand splits (3 products, FP32 accumulate)."""

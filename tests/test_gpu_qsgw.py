@@ -46,3 +46,33 @@ def test_qsgw_potential_matches_oracle(h, reg, nocc, nvir, naux, nmom_max, seed)
     got = h.mgw_qsgw_potential(nmo, nblk, rh, rp, torch.from_numpy(eps).cuda(), hole, part, reg, 1e-3, 100.0)
     got = got.cpu().numpy()
     assert np.linalg.norm(got - ref) < 1e-10 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("reg", ["eta", "srg"])
+@pytest.mark.parametrize("precision", ["fp64", "fp64_tc"])
+@pytest.mark.parametrize("nocc,nvir,naux,nmom_max,seed,scale", [(3, 5, 12, 2, 7, 3.0), (4, 13, 40, 3, 9, 2.5)])
+def test_qsgw_loop_reaches_the_oracles_fixed_point(h, reg, precision, nocc, nvir, naux, nmom_max, seed, scale):
+    """mgw_qsgw_step repeated to convergence (Sec. III D, Eq. 35 with the
+    static potential of Eqs. 36-39) against the oracle's qsGW loop: the same
+    energies, density and field at the fixed point (the DIIS histories differ,
+    the fixed point does not)."""
+    from paper_2504_17439_gb300 import driver, mgw
+
+    eps = mgw_inputs.orbital_energies(nocc, nvir, seed)
+    L = mgw_inputs.df_tensor(naux, nocc + nvir, seed) * scale
+    hc = orc.hf_core_hamiltonian(eps, L, nocc)
+    ref = orc.qsgw(hc, L, eps, nocc, nmom_max, reg=reg, delta=1e-3, srg_s=100.0, conv=1e-10)
+    assert ref["converged"]
+    o = mgw.options(precision=mgw.MGW_FP64 if precision == "fp64" else mgw.MGW_FP64_TC)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    r = driver.qsgw(h, dev(hc), dev(L), dev(eps), nocc, nmom_max, reg=reg, delta=1e-3, srg_s=100.0, opts=o,
+                    conv=1e-10)
+    assert r["converged"], r["history"]
+    e, C, F, V = (r[k].cpu().numpy() for k in ("eps", "C", "F", "V"))
+    assert np.abs(e - ref["eps"]).max() < 1e-8
+    rho = 2.0 * C[:, :nocc] @ C[:, :nocc].T
+    rho_ref = 2.0 * ref["C"][:, :nocc] @ ref["C"][:, :nocc].T
+    assert np.abs(rho - rho_ref).max() < 1e-8
+    assert np.abs(F - ref["F"]).max() < 1e-8 and np.abs(V - ref["V"]).max() < 1e-8
+    # the GPU's own fixed point: F C = C diag(eps)
+    assert np.abs(F @ C - C * e[None, :]).max() < 1e-9

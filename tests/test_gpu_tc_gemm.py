@@ -56,3 +56,23 @@ def test_fp64_emulated_gemm_zero_rows(h):
     ref = A @ B.T
     assert np.abs(C - ref).max() <= 1e-15 * np.abs(ref).max()
     assert np.all(C[np.arange(130) != 5] == 0)
+
+
+def test_bounded_wait_gives_up_and_the_handle_stays_usable(h):
+    """A wait that nothing satisfies ends after its limit with MGW_ERR_TIMEOUT
+    (not a hang, not a fault), and the next tensor-core call on the same
+    handle and stream is correct."""
+    import time
+
+    from paper_2504_17439_gb300 import mgw
+
+    t0 = time.perf_counter()
+    with pytest.raises(mgw.MgwError) as e:
+        h.mgw_selftest_bounded_wait(0.05)
+    dt = time.perf_counter() - t0
+    assert e.value.status == -7 and "timed out" in str(e.value)
+    assert 0.04 < dt < 5.0, dt
+    g = np.random.default_rng(9)
+    A, B = g.standard_normal((200, 300)), g.standard_normal((150, 300))
+    C = h.mgw_gemm_fp64_emu(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()).cpu().numpy()
+    assert (np.abs(C - A @ B.T) / (np.abs(A) @ np.abs(B).T)).max() < 1e-15
