@@ -508,6 +508,19 @@ mgw_status mgw_gemm_fp64_emu(mgw_handle* h, int M, int N, int K,
                              const double* A, const double* B, double* C);
 
 /*
+ * mgw_gemm_mixed -- C = A B'^T on the BF16 tensor cores, B' = B rounded to one
+ * fixed-point grid (multiples of 2^(e-16), max |B| < 2^(e-1)), the product
+ * of the MGW_MIXED precision: B' as two BF16 digits, A as seven per-row
+ * digits, the 13 digit products above 2^-64 of the top, each exact; the K
+ * loop runs in chunks of 128 so that each digit tile loaded serves every
+ * product it takes part in.  Error against the exact A B'^T: a few units of
+ * 2^-53 times sum_k |A_ik||B'_jk|.  Not in the paper.
+ *   A [M][K], B [N][K] in (FP64, row-major);  C [M][N] out (FP64)
+ */
+mgw_status mgw_gemm_mixed(mgw_handle* h, int M, int N, int K,
+                          const double* A, const double* B, double* C);
+
+/*
  * mgw_gemm_bf16x3 -- C = A B^T on the tensor cores (tcgen05, TMA, TMEM):
  * each FP64 operand is split as x = hi + lo with hi = bf16(x),
  * lo = bf16(x - hi), and C accumulates hi*hi + hi*lo + lo*hi in FP32, then is

@@ -401,6 +401,10 @@ mgw_status gemm_tn(mgw_handle* h, long M, long N, long K, double alpha, const do
 // Cholesky factor + solve).  Row-major symmetric matrices; on return of
 // syevd, row j of `a` holds eigenvector j (eigenvalues ascending in w).
 mgw_status syevd(mgw_handle* h, int n, double* a, double* w);
+// Eigenvalues E [n] (ascending) of the symmetric H [n][n] and the first
+// nrows rows of its eigenvectors, chi[p][a] = X_pa (ld ldchi); H is
+// overwritten (tridiag.cu)
+mgw_status eig_physical_rows(mgw_handle* h, int n, int nrows, double* H, double* E, double* chi, long ldchi);
 mgw_status potrf_potrs(mgw_handle* h, int n, double* a, int nrhs, double* b, bool* not_pd);
 
 // Small elementwise kernels

@@ -1,6 +1,7 @@
 // Digit slicing for the FP64-accurate tensor-core GEMM, tensor maps, and
 // the public entry point mgw_gemm_fp64_emu.
 #include "ozaki.h"
+#include "ozaki_mixed.h"
 #include "tc_gemm.h"
 
 #include <cuda_bf16.h>
@@ -419,4 +420,59 @@ extern "C" mgw_status mgw_gemm_fp64_emu(mgw_handle* h, int M, int N, int K, cons
   MGW_TRY((ozaki_launch(h, ma, mb, sa.exps, sb.exps, M, N, K, ARowsPlain{}, EpiStoreRows{C, N}, dstatus,
                         "gemm_fp64_emu")));
   return tc::check_tc_status(h, dstatus, "mgw_gemm_fp64_emu");
+}
+
+namespace mgw {
+namespace oz {
+mgw_status gemm_fp64_tc_nn(mgw_handle* h, int M, int N, int K, const double* A, long lda, const double* B, long ldb,
+                           double* C, long ldc, const char* what) {
+  if (M < 1 || N < 1 || K < 1) return MGW_OK;
+  Arena ar;
+  double *da, *db, *st;
+  ar.add(&da, sliced_doubles(M, K));
+  ar.add(&db, sliced_doubles(N, K));
+  ar.add(&st, 1);
+  MGW_TRY(ar.commit(h));
+  Sliced sa, sb;
+  place_sliced(da, M, K, sa);
+  place_sliced(db, N, K, sb);
+  int* dstatus = reinterpret_cast<int*>(st);
+  MGW_CUDA(h, cudaMemsetAsync(dstatus, 0, sizeof(int), h->stream));
+  MGW_TRY(slice_rows(h, M, K, A, lda, sa));
+  MGW_TRY(slice_cols(h, N, K, B, ldb, sb));
+  CUtensorMap ma, mb;
+  MGW_TRY(digit_map(h, &ma, sa, BM));
+  MGW_TRY(digit_map(h, &mb, sb, BN));
+  MGW_TRY((ozaki_launch(h, ma, mb, sa.exps, sb.exps, M, N, K, ARowsPlain{}, EpiStoreRows{C, ldc}, dstatus, what)));
+  return tc::check_tc_status(h, dstatus, what);
+}
+}  // namespace oz
+}  // namespace mgw
+
+extern "C" mgw_status mgw_gemm_mixed(mgw_handle* h, int M, int N, int K, const double* A, const double* B,
+                                     double* C) {
+  if (!h) return MGW_ERR_ARG;
+  if (M < 1 || N < 1 || K < 1 || !A || !B || !C) return fail(h, MGW_ERR_ARG, "mgw_gemm_mixed: bad arguments");
+  MGW_CUDA(h, cudaSetDevice(h->device));
+  Arena ar;
+  double *da, *db, *st;
+  ar.add(&da, sliced_doubles(M, K));
+  ar.add(&db, sliced_doubles(N, K, kGridSlices));
+  ar.add(&st, 3);
+  MGW_TRY(ar.commit(h));
+  Sliced sa, sb;
+  place_sliced(da, M, K, sa);
+  place_sliced(db, N, K, sb, kGridSlices);
+  int* dstatus = reinterpret_cast<int*>(st);
+  int* gexp = reinterpret_cast<int*>(st + 2);
+  MGW_CUDA(h, cudaMemsetAsync(dstatus, 0, sizeof(int), h->stream));
+  MGW_TRY(slice_rows(h, M, K, A, K, sa));
+  MGW_TRY(global_exponent(h, (long)N * K, B, reinterpret_cast<unsigned long long*>(st + 1), gexp));
+  MGW_TRY(slice_rows_grid(h, N, K, B, K, gexp, sb));
+  CUtensorMap ma, mb;
+  MGW_TRY(digit_map(h, &ma, sa, BM));
+  MGW_TRY(digit_map(h, &mb, sb, BN));
+  MGW_TRY((ozaki_mixed_launch<true>(h, ma, mb, sa.exps, sb.exps, M, N, K, ARowsPlain{}, EpiStoreRows{C, N}, dstatus,
+                                    "gemm_mixed")));
+  return tc::check_tc_status(h, dstatus, "mgw_gemm_mixed");
 }

@@ -572,6 +572,11 @@ inline int best_split(long kept, long K, int sms) {
   }
   return best;
 }
+// C [M][N] (ldc) = A [M][K] (lda) B [K][N] (ldb), row-major, as an
+// FP64-accurate digit-sliced product (28 products); synchronises to read the
+// wait status
+mgw_status gemm_fp64_tc_nn(mgw_handle* h, int M, int N, int K, const double* A, long lda, const double* B, long ldb,
+                           double* C, long ldc, const char* what);
 // sum of the split buffers: out[i] = (accumulate ? out[i] : 0) + sum_z part[z count + i]
 mgw_status reduce_splits(mgw_handle* h, long count, int nsplit, const double* part, double* out, int accumulate);
 

@@ -1,5 +1,6 @@
-// Upfolded Hamiltonian (Eq. 9), its diagonalisation, QP energies (Eq. 34),
-// Aufbau chemical potential and correlated density (Eq. 40), FP64.
+// Upfolded Hamiltonian (Eq. 9), its eigenvalues and the physical rows of its
+// eigenvectors (tridiag.cu: only those rows are formed), QP energies
+// (Eq. 34), Aufbau chemical potential and correlated density (Eq. 40), FP64.
 #include "mgw_internal.h"
 
 #include <cmath>
@@ -21,36 +22,28 @@ __global__ void k_place(int rows, int cols, const double* src, long lds, double*
   if (mirror) H[(c0 + j) * ld + r0 + i] = v;
 }
 
-// weight[a] = sum_{p < nmo} X[a][p]^2 (rows of X are eigenvectors); chi[p][a] = X[a][p]
-__global__ void k_weights(int dim, int nmo, const double* X, double* weight, double* chi) {
-  int a = blockIdx.x;
+// weight[a] = sum_p chi[p][a]^2 (chi: the physical rows of the eigenvectors)
+__global__ void k_weights(int dim, int nmo, const double* __restrict__ chi, double* weight) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= dim) return;
-  __shared__ double s[256];
   double acc = 0.0;
-  for (int p = threadIdx.x; p < nmo; p += blockDim.x) {
-    double v = X[(long)a * dim + p];
+  for (int p = 0; p < nmo; ++p) {
+    const double v = chi[(long)p * dim + a];
     acc += v * v;
-    if (chi) chi[(long)p * dim + a] = v;
   }
-  s[threadIdx.x] = acc;
-  __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) weight[a] = s[0];
+  weight[a] = acc;
 }
 
-// eps_qp[p] = E[argmax_a X[a][p]^2], ties to the lowest a
-__global__ void k_qp_argmax(int dim, int nmo, const double* X, const double* E, double* eps_qp) {
-  int p = blockIdx.x;
+// eps_qp[p] = E[argmax_a chi[p][a]^2], ties to the lowest a
+__global__ void k_qp_argmax(int dim, int nmo, const double* __restrict__ chi, const double* E, double* eps_qp) {
+  const int p = blockIdx.x;
   if (p >= nmo) return;
   __shared__ double sv[256];
   __shared__ int si[256];
   double best = -1.0;
   int bi = 0x7fffffff;
   for (int a = threadIdx.x; a < dim; a += blockDim.x) {
-    double v = X[(long)a * dim + p];
+    double v = chi[(long)p * dim + a];
     v *= v;
     if (v > best || (v == best && a < bi)) { best = v; bi = a; }
   }
@@ -142,11 +135,13 @@ extern "C" mgw_status mgw_qp_solve(mgw_handle* h, const mgw_options* o, int nmo,
     }
     off += (long)nblk * r;
   }
-  // eigen-decomposition; rows of H become eigenvectors, E ascending
-  MGW_TRY(syevd(h, (int)dim, H, E));
-  k_weights<<<(unsigned)dim, 256, 0, h->stream>>>((int)dim, nmo, H, weight, chi_phys);
+  // eigenvalues (ascending) and the physical rows of the eigenvectors only
+  double* chi = chi_phys;
+  if (!chi) MGW_TRY(slot_buffer(h, 84, (size_t)nmo * dim, &chi));
+  MGW_TRY(eig_physical_rows(h, (int)dim, nmo, H, E, chi, dim));
+  k_weights<<<(unsigned)((dim + 127) / 128), 128, 0, h->stream>>>((int)dim, nmo, chi, weight);
   MGW_TRY(check_launch(h, "weights"));
-  k_qp_argmax<<<nmo, 256, 0, h->stream>>>((int)dim, nmo, H, E, eps_qp);
+  k_qp_argmax<<<nmo, 256, 0, h->stream>>>((int)dim, nmo, chi, E, eps_qp);
   MGW_TRY(check_launch(h, "qp_argmax"));
   k_aufbau<<<1, 32, 0, h->stream>>>((int)dim, E, weight, nelec, scal);
   MGW_TRY(check_launch(h, "aufbau"));
@@ -161,8 +156,8 @@ extern "C" mgw_status mgw_qp_solve(mgw_handle* h, const mgw_options* o, int nmo,
     if (m == 0) {
       MGW_CUDA(h, cudaMemsetAsync(rho, 0, sizeof(double) * n2, h->stream));
     } else {
-      // rho[p][q] = 2 sum_{a<m} X[a][p] X[a][q]
-      MGW_TRY(gemm_tn(h, nmo, nmo, m, 2.0, H, dim, H, dim, 0.0, rho, nmo));
+      // rho[p][q] = 2 sum_{a<m} chi[p][a] chi[q][a]
+      MGW_TRY(gemm_nt(h, nmo, nmo, m, 2.0, chi, dim, chi, dim, 0.0, rho, nmo));
     }
   }
   return MGW_OK;

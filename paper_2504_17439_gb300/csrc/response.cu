@@ -20,6 +20,7 @@
 // cores as well; the Cholesky solves of each node stay FP64 (cuSOLVER).
 #include "mgw_internal.h"
 #include "ozaki.h"
+#include "ozaki_mixed.h"
 #include "tc_gemm.h"
 
 #include <algorithm>
@@ -324,8 +325,7 @@ extern "C" mgw_status mgw_response_moments(mgw_handle* h, const mgw_options* o, 
     auto launch = [&](const CUtensorMap& ma, const CUtensorMap& mb, const int* ea, const int* eb, int M, int N,
                       int K, auto epi, const char* what, int nsp) {
       if (mixed)
-        return oz::ozaki_launch<oz::kSlices, oz::kGridSlices>(h, ma, mb, ea, eb, M, N, K, oz::ARowsPlain{}, epi,
-                                                              dstatus, what, nsp);
+        return oz::ozaki_mixed_launch<true>(h, ma, mb, ea, eb, M, N, K, oz::ARowsPlain{}, epi, dstatus, what, nsp);
       return oz::ozaki_launch(h, ma, mb, ea, eb, M, N, K, oz::ARowsPlain{}, epi, dstatus, what, nsp);
     };
     for (int n = 0; n < nmom; ++n) {

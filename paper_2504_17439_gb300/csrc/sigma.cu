@@ -25,6 +25,7 @@
 // to FP64 accuracy; L' differs from L by at most 2^-17 of max |L|.
 #include "mgw_internal.h"
 #include "ozaki.h"
+#include "ozaki_mixed.h"
 #include "tc_gemm.h"
 
 #include <algorithm>
@@ -205,10 +206,8 @@ extern "C" mgw_status mgw_sigma_moments(mgw_handle* h, const mgw_options* o, int
         MGW_TRY(oz::digit_map(h, &ml, sl, oz::BN));
         auto launch_y = [&](auto epi) {
           if (mixed)
-            return oz::ozaki_launch<oz::kSlices, oz::kGridSlices>(h, mw, ml, sw.exps, sl.exps,
-                                                                  (int)(ngroups_t * 128), (int)ncol, naux,
-                                                                  oz::ARowsPlain{}, epi, dstatus,
-                                                                  "sigma_y_binomial_tc");
+            return oz::ozaki_mixed_launch<true>(h, mw, ml, sw.exps, sl.exps, (int)(ngroups_t * 128), (int)ncol,
+                                                naux, oz::ARowsPlain{}, epi, dstatus, "sigma_y_binomial_tc");
           return oz::ozaki_launch(h, mw, ml, sw.exps, sl.exps, (int)(ngroups_t * 128), (int)ncol, naux,
                                   oz::ARowsPlain{}, epi, dstatus, "sigma_y_binomial_tc");
         };
@@ -248,9 +247,8 @@ extern "C" mgw_status mgw_sigma_moments(mgw_handle* h, const mgw_options* o, int
         auto launch_g2 = [&](const oz::FSigmaN& f, int nsp) {
           const oz::EpiElem<oz::FSigmaN> epi{f};
           if (mixed)
-            return oz::ozaki_launch<oz::kGridSlices, oz::kSlices>(h, ma2, mz2, sa2.exps, sz2.exps, nmo, nmom * nmo,
-                                                                  (int)K2, oz::ARowsPlain{}, epi, dstatus,
-                                                                  "sigma_gemm2_tc", nsp);
+            return oz::ozaki_mixed_launch<false>(h, ma2, mz2, sa2.exps, sz2.exps, nmo, nmom * nmo, (int)K2,
+                                                 oz::ARowsPlain{}, epi, dstatus, "sigma_gemm2_tc", nsp);
           return oz::ozaki_launch(h, ma2, mz2, sa2.exps, sz2.exps, nmo, nmom * nmo, (int)K2, oz::ARowsPlain{}, epi,
                                   dstatus, "sigma_gemm2_tc", nsp);
         };

@@ -102,6 +102,7 @@ _SIGS = {
     "mgw_gemm_bf16x3": [_I, _I, _I, _P, _P, _P],
     "mgw_gemm_fp64_emu": [_I, _I, _I, _P, _P, _P],
     "mgw_selftest_bounded_wait": [_D],
+    "mgw_gemm_mixed": [_I, _I, _I, _P, _P, _P],
     "mgw_response_moments": [_P, _I, _I, _I, _I, _P, _P, _P],
     "mgw_sigma_moments": [_P, _I, _I, _I, _I, _P, _P, _P, _P, _P],
     "mgw_block_lanczos": [_P, _I, _I, _P, _P, _P, _P, ctypes.POINTER(_I)],
@@ -401,6 +402,15 @@ class Handle:
         C = C if C is not None else torch.empty((M, N), dtype=torch.float64, device=A.device)
         self._check(self._lib.mgw_gemm_fp64_emu(self._h, M, N, K, _ptr(A, (M, K), "A"), _ptr(B, (N, K), "B"),
                                                 _ptr(C, (M, N), "C")))
+        return C
+
+    def mgw_gemm_mixed(self, A, B, C=None):
+        """C = A B'^T, B' = B on its 16-bit grid (two digits), A at seven digits, every product exact."""
+        M, K = A.shape
+        N = B.shape[0]
+        C = C if C is not None else torch.empty((M, N), dtype=torch.float64, device=A.device)
+        self._check(self._lib.mgw_gemm_mixed(self._h, M, N, K, _ptr(A, (M, K), "A"), _ptr(B, (N, K), "B"),
+                                             _ptr(C, (M, N), "C")))
         return C
 
     def mgw_selftest_bounded_wait(self, limit_s):

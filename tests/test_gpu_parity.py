@@ -298,3 +298,35 @@ def test_bad_arguments_return_status(h):
         h.mgw_response_moments(mgw.options(screening=1, nquad=7), 1, 1, 1, 2, dev(np.array([-1.0, 1.0])),
                                dev(np.ones((1, 1))))
     assert ei.value.status == -1
+
+
+def test_qp_solve_degenerate_poles(h):
+    """Exactly degenerate poles: a physical block with a repeated eigenvalue
+    and an uncoupled chain of two identical 2 x 2 blocks.  Degenerate
+    eigenvectors are fixed only up to a rotation, so compare what is unique:
+    every pole, the summed physical weight of each degenerate group, and the
+    density."""
+    from paper_2504_17439_gb300 import mgw
+
+    nmo, nblk = 4, 2
+    g = np.random.default_rng(4)
+    Qf, _ = np.linalg.qr(g.standard_normal((nmo, nmo)))
+    fock = Qf @ np.diag([-1.0, -1.0, 0.5, 2.0]) @ Qf.T
+    r = 2
+    coup = np.zeros((nmo, nmo))
+    alpha = np.zeros((nblk, nmo, nmo))
+    alpha[0, :r, :r] = np.diag([-1.0, -1.0])
+    alpha[1, :r, :r] = np.diag([3.0, 3.0])
+    beta = np.zeros((nblk - 1, nmo, nmo))
+    beta[0, :r, :r] = 0.2 * np.eye(r)
+    hole = (coup, alpha[:, :r, :r], beta[:, :r, :r])
+    ref = orc.qp_solve(fock, (coup[:, :r],) + hole[1:], (np.zeros((nmo, 0)), np.zeros((nblk, 0, 0)),
+                                                        np.zeros((nblk - 1, 0, 0))), 4.0)
+    got = h.mgw_qp_solve(mgw.options(), nmo, nblk, r, 0, dev(fock), (dev(coup), dev(alpha), dev(beta)),
+                         (None, None, None), 0.0, 4.0)  # N = 4 fills the degenerate pair whole: rho is unique
+    E, w = host(got["E"]), host(got["weight"])
+    assert np.abs(E - ref["E"]).max() < 1e-12
+    groups = np.split(np.arange(E.size), np.where(np.diff(ref["E"]) > 1e-6)[0] + 1)
+    for grp in groups:
+        assert abs(w[grp].sum() - ref["weight"][grp].sum()) < 1e-10
+    assert np.abs(host(got["rho"]) - ref["rho"]).max() < 1e-10

@@ -76,3 +76,25 @@ def test_bounded_wait_gives_up_and_the_handle_stays_usable(h):
     A, B = g.standard_normal((200, 300)), g.standard_normal((150, 300))
     C = h.mgw_gemm_fp64_emu(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()).cpu().numpy()
     assert (np.abs(C - A @ B.T) / (np.abs(A) @ np.abs(B).T)).max() < 1e-15
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 96, 64), (300, 520, 200), (1, 1, 1), (257, 17, 1000), (512, 384, 4800),
+                                   (130, 140, 2500), (200, 300, 100)])
+def test_mixed_gemm_is_exact_for_the_rounded_operand(h, M, N, K):
+    """The mixed-precision product (chunked, tile-reusing kernel): A at seven
+    digits against B rounded to its 16-bit grid (the oracle's
+    fixed_point_grid), within a few 2^-53 of sum_k |A||B'| -- an FP64 GEMM's
+    own bound on the product with the rounded operand; K spans odd chunk
+    counts and a partial last chunk."""
+    from oracle import mgw_oracle as orc
+
+    g = np.random.default_rng(M * 3 + N * 7 + K)
+    A = g.standard_normal((M, K)) * np.exp2(g.integers(-20, 20, (M, 1)))
+    B = g.standard_normal((N, K))
+    A[:, :: max(1, K // 7)] *= 1e-9
+    C = h.mgw_gemm_mixed(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()).cpu().numpy()
+    Bq = orc.fixed_point_grid(B)
+    ref = A @ Bq.T
+    scale = np.abs(A) @ np.abs(Bq).T
+    err = np.abs(C - ref) / np.where(scale > 0, scale, 1.0)
+    assert err.max() < 8 * 2.0**-52, err.max()
