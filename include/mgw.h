@@ -164,6 +164,31 @@ mgw_status mgw_sigma_moments(mgw_handle* h, const mgw_options* o,
                              double* sig_hole, double* sig_part);
 
 /*
+ * mgw_sigma_moments_x -- mgw_sigma_moments over a Green's-function space of
+ * its own: x = 0..nx-1 with energies eps_x, the first nhole of them holes,
+ * and Lx [naux][nx][nmo] holding L_{P,x q} in row x of slab P (for the
+ * orbitals themselves nx = nmo and Lx = L).  The space of the quasi-molecular
+ * orbitals of scGW / G0W (Algorithm 5), where x runs over every pole of H~.
+ *   eps_x [nx], Lx [naux][nx][nmo], Wmom [nmom][naux][naux] in;
+ *   sig_hole, sig_part [nmom][nmo][nmo] out.  Precisions as mgw_sigma_moments.
+ */
+mgw_status mgw_sigma_moments_x(mgw_handle* h, const mgw_options* o, int nmo, int nx, int nhole, int naux, int nmom,
+                               const double* eps_x, const double* Lx, const double* Wmom,
+                               double* sig_hole, double* sig_part);
+
+/*
+ * mgw_qmo_tensors -- the DF tensor carried to the quasi-molecular orbitals of
+ * H~ (Algorithm 5, reading S1: the map is the physical rows chi_px of H~'s
+ * eigenvectors), with the first m poles occupied (Eq. 40, reading S2):
+ *   Lt [naux][nx][nmo], Lt[Q][x][p] = sum_q L[Q][p][q] chi[q][x]  (for mgw_sigma_moments_x)
+ *   Via [naux][m][nx-m], Via[Q][i][a] = sum_p chi[p][i] Lt[Q][m+a][p]  (for mgw_response_moments)
+ * L [naux][nmo][nmo] symmetric slabs, chi [nmo][nx] as written by
+ * mgw_qp_solve.  FP64 GEMMs.  Via is not written when m is 0 or nx.
+ */
+mgw_status mgw_qmo_tensors(mgw_handle* h, int nmo, int naux, int nx, int m, const double* L, const double* chi,
+                           double* Lt, double* Via);
+
+/*
  * mgw_block_lanczos -- moment-conserving upfolding of one sector (Eqs. 9-10):
  * coupling S0^(1/2), diagonal blocks alpha_0..alpha_{nblk-1} and
  * off-diagonal blocks beta_1..beta_{nblk-1} of a block tridiagonal T with
@@ -506,6 +531,35 @@ mgw_status mgw_mlp_adam(mgw_handle* h, long n, float* params, unsigned short* wb
  */
 mgw_status mgw_gemm_fp64_emu(mgw_handle* h, int M, int N, int K,
                              const double* A, const double* B, double* C);
+
+/*
+ * The DF tensor on the mixed precision's grid, held as 16-bit integers: for
+ * systems whose FP64 tensor does not fit the GPU (or the host) -- 2147
+ * orbitals and 8588 auxiliary functions make 317 GB in FP64, 79 GB here.
+ *   mgw_grid_exponent -- e with absmax < 2^(e-1), i.e. floor(log2 absmax) + 2
+ *     (0 for absmax 0); the grid of MGW_MIXED is the multiples of 2^(e-16).
+ *   mgw_df_absmax -- max |L| over `count` consecutive FP64 values (device),
+ *     written to *absmax_host (synchronises): the maxima of the pieces of a
+ *     tensor give its grid.
+ *   mgw_df_quantize -- Lq = round(L 2^(16-e)) (ties away from zero) for
+ *     `count` consecutive values: any slab range, so a tensor is quantized
+ *     piece by piece as it is produced.  A value with |L| >= 2^(e-1) is stored
+ *     as 0 and, when overflow_host is given, reported there (the call then
+ *     synchronises and returns MGW_ERR_ARG).
+ *   mgw_response_moments_q, mgw_sigma_moments_q -- mgw_response_moments (TDA)
+ *     and mgw_sigma_moments in the MGW_MIXED precision (whatever o->precision
+ *     says) from Lq [naux][nmo][nmo] with exponent e; the response takes V'
+ *     from Lq's particle-hole block directly.  The results equal those of the
+ *     FP64 calls on the tensor L' = Lq 2^(e-16).
+ */
+int mgw_grid_exponent(double absmax);
+mgw_status mgw_df_absmax(mgw_handle* h, long count, const double* L, double* absmax_host);
+mgw_status mgw_df_quantize(mgw_handle* h, long count, const double* L, int e, short* Lq, int* overflow_host);
+mgw_status mgw_response_moments_q(mgw_handle* h, const mgw_options* o, int nocc, int nvir, int naux, int nmom,
+                                  const double* eps_W, const short* Lq, int e, double* Wmom);
+mgw_status mgw_sigma_moments_q(mgw_handle* h, const mgw_options* o, int nocc, int nvir, int naux, int nmom,
+                               const double* eps_G, const short* Lq, int e, const double* Wmom,
+                               double* sig_hole, double* sig_part);
 
 /*
  * mgw_gemm_mixed -- C = A B'^T on the BF16 tensor cores, B' = B rounded to one

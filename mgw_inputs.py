@@ -61,6 +61,9 @@ WORKLOADS = {
     "g0w0-nmo200-naux800": dict(shape=Shape(30, 170, 800, 7), seed=SEED_BASE + 300),
     # pigment-molecule scale, mixed-precision workload
     "g0w0-nmo1200-naux4800": dict(shape=Shape(240, 960, 4800, 7), seed=SEED_BASE + 200),
+    # chlorophyll-A scale (2147 orbitals, 482 electrons, naux = 4 nmo): 317 GB
+    # in FP64, produced slab by slab (df_slab) and never held whole
+    "g0w0-nmo2147-naux8588": dict(shape=Shape(241, 1906, 8588, 7), seed=SEED_BASE + 600),
 }
 
 

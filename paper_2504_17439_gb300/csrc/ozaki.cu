@@ -7,6 +7,8 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cmath>
+#include <cstring>
 
 namespace mgw {
 namespace oz {
@@ -296,6 +298,89 @@ mgw_status slice_gather_grid(mgw_handle* h, long rows, long K, const double* X, 
   return check_launch(h, "gather_digits_grid");
 }
 
+// The same gather from a tensor already on its grid, held as 16-bit
+// integers q (value q 2^(e-16)): the two digits come straight from q, exactly
+// as digits_of<2> gives them for the value, and every row takes exponent e.
+__global__ void k_gather_digits_q(long rows, long K, const short* __restrict__ X, Gather g, int e,
+                                  __nv_bfloat16* dig, long ld, int* exps) {
+  __shared__ __align__(4) __nv_bfloat16 sd[kGridSlices][32][66];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long r0 = blockIdx.x * 32L, r = r0 + lane;
+  const long k0 = blockIdx.y * 64L;
+  if (r < rows && blockIdx.y == 0) exps[r] = e;
+  const short* xr = r < rows ? X + (r / g.rdiv) * g.rhi + (r % g.rdiv) * g.rlo : X;
+  KWalk kw(k0 + w, g);
+#pragma unroll 2
+  for (int kk = w; kk < 64; kk += 8) {
+    const long k = k0 + kk;
+    const int q = (r < rows && k < K) ? (int)xr[kw.off()] : 0;
+    kw.step(8);
+    const int d2 = ((q + 128) & 255) - 128;
+    const int d1 = (q - d2) >> 8;
+    sd[0][lane][kk] = __float2bfloat16_rn((float)d1);
+    sd[1][lane][kk] = __float2bfloat16_rn((float)d2 * 0x1p-8f);
+  }
+  __syncthreads();
+  const long plane = rows * ld;
+  for (int i = threadIdx.x; i < kGridSlices * 32 * 32; i += 256) {
+    const int s = i / (32 * 32), rr = (i / 32) % 32, kp = (i % 32) * 2;
+    if (r0 + rr < rows && k0 + kp < ld)
+      *reinterpret_cast<uint32_t*>(dig + s * plane + (r0 + rr) * ld + k0 + kp) =
+          *reinterpret_cast<const uint32_t*>(&sd[s][rr][kp]);
+  }
+}
+
+mgw_status slice_gather_q(mgw_handle* h, long rows, long K, const short* X, const Gather& g, int e, Sliced& out) {
+  ProfSpan span(h, "slice_gather_grid");
+  if (out.ns != kGridSlices) return fail(h, MGW_ERR_ARG, "slice_gather_q: %d-digit planes", out.ns);
+  if (rows <= 0) return MGW_OK;
+  if (out.ld == 0) {
+    MGW_CUDA(h, cudaMemsetAsync(out.exps, 0, sizeof(int) * rows, h->stream));
+    return MGW_OK;
+  }
+  k_gather_digits_q<<<dim3((unsigned)((rows + 31) / 32), (unsigned)(out.ld / 64)), 256, 0, h->stream>>>(
+      rows, K, X, g, e, static_cast<__nv_bfloat16*>(out.digits), out.ld, out.exps);
+  return check_launch(h, "gather_digits_q");
+}
+
+// out[r][k] = q 2^(e-16) for element (r, k) of a gathered 16-bit grid tensor
+__global__ void k_dequantize_gather(long rows, long K, const short* __restrict__ X, Gather g, int e, double* out) {
+  const double unit = ldexp(1.0, e - 8 * kGridSlices);
+  const long total = rows * K;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    const long r = i / K, k = i % K;
+    out[i] = (double)X[(r / g.rdiv) * g.rhi + (r % g.rdiv) * g.rlo + (k / g.kdiv) * g.khi + (k % g.kdiv) * g.klo] * unit;
+  }
+}
+
+mgw_status dequantize_gather(mgw_handle* h, long rows, long K, const short* X, const Gather& g, int e, double* out) {
+  if (rows <= 0 || K <= 0) return MGW_OK;
+  k_dequantize_gather<<<(unsigned)std::min<long>((rows * K + 255) / 256, 152L * 16), 256, 0, h->stream>>>(
+      rows, K, X, g, e, out);
+  return check_launch(h, "dequantize_gather");
+}
+
+// Lq = round(L 2^(16 - e)) (ties away from zero) as 16-bit integers; a value
+// with |L| >= 2^(e-1) (outside the grid's range) raises *overflow
+__global__ void k_quantize(long n, const double* __restrict__ L, int e, short* Lq, int* overflow) {
+  const double lim = ldexp(1.0, e - 1);
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const double x = L[i];
+    if (!(fabs(x) < lim)) {
+      atomicOr(overflow, 1);
+      Lq[i] = 0;
+      continue;
+    }
+    Lq[i] = (short)fixed_of(x, e, 8 * kGridSlices);
+  }
+}
+
+mgw_status quantize(mgw_handle* h, long n, const double* L, int e, short* Lq, int* overflow) {
+  if (n <= 0) return MGW_OK;
+  k_quantize<<<(unsigned)std::min<long>((n + 255) / 256, 152L * 16), 256, 0, h->stream>>>(n, L, e, Lq, overflow);
+  return check_launch(h, "quantize");
+}
+
 mgw_status slice_cols(mgw_handle* h, long rows, long K, const double* X, long ldx, Sliced& out) {
   // element (r, k) = X[k * ldx + r]: a gather with undivided row and k indices
   return slice_gather(h, rows, K, X, Gather{rows + 1, 0, 1, K + 1, 0, ldx}, out);
@@ -427,12 +512,12 @@ namespace oz {
 mgw_status gemm_fp64_tc_nn(mgw_handle* h, int M, int N, int K, const double* A, long lda, const double* B, long ldb,
                            double* C, long ldc, const char* what) {
   if (M < 1 || N < 1 || K < 1) return MGW_OK;
-  Arena ar;
+  // slot buffers, not the workspace arena: callers run this inside calls that
+  // hold arena pointers, and growing the arena would move them
   double *da, *db, *st;
-  ar.add(&da, sliced_doubles(M, K));
-  ar.add(&db, sliced_doubles(N, K));
-  ar.add(&st, 1);
-  MGW_TRY(ar.commit(h));
+  MGW_TRY(slot_buffer(h, 85, sliced_doubles(M, K), &da));
+  MGW_TRY(slot_buffer(h, 86, sliced_doubles(N, K), &db));
+  MGW_TRY(slot_buffer(h, 87, 1, &st));
   Sliced sa, sb;
   place_sliced(da, M, K, sa);
   place_sliced(db, N, K, sb);
@@ -475,4 +560,48 @@ extern "C" mgw_status mgw_gemm_mixed(mgw_handle* h, int M, int N, int K, const d
   MGW_TRY((ozaki_mixed_launch<true>(h, ma, mb, sa.exps, sb.exps, M, N, K, ARowsPlain{}, EpiStoreRows{C, N}, dstatus,
                                     "gemm_mixed")));
   return tc::check_tc_status(h, dstatus, "mgw_gemm_mixed");
+}
+
+extern "C" int mgw_grid_exponent(double absmax) {
+  if (!(absmax > 0.0) || !std::isfinite(absmax)) return 0;
+  return std::ilogb(absmax) + 2;  // absmax < 2^(e-1)
+}
+
+extern "C" mgw_status mgw_df_absmax(mgw_handle* h, long count, const double* L, double* absmax_host) {
+  if (!h) return MGW_ERR_ARG;
+  if (count < 0 || (count > 0 && !L) || !absmax_host) return fail(h, MGW_ERR_ARG, "mgw_df_absmax: bad arguments");
+  MGW_CUDA(h, cudaSetDevice(h->device));
+  Arena ar;
+  double* st;
+  ar.add(&st, 2);
+  MGW_TRY(ar.commit(h));
+  MGW_TRY(global_exponent(h, count, L, reinterpret_cast<unsigned long long*>(st), reinterpret_cast<int*>(st + 1)));
+  unsigned long long bits = 0;
+  MGW_CUDA(h, cudaMemcpyAsync(&bits, st, sizeof bits, cudaMemcpyDeviceToHost, h->stream));
+  MGW_CUDA(h, cudaStreamSynchronize(h->stream));
+  double v;
+  std::memcpy(&v, &bits, sizeof v);
+  *absmax_host = v;
+  return MGW_OK;
+}
+
+extern "C" mgw_status mgw_df_quantize(mgw_handle* h, long count, const double* L, int e, short* Lq,
+                                      int* overflow_host) {
+  if (!h) return MGW_ERR_ARG;
+  if (count < 0 || (count > 0 && (!L || !Lq)) || e < -1000 || e > 1000)
+    return fail(h, MGW_ERR_ARG, "mgw_df_quantize: bad arguments");
+  MGW_CUDA(h, cudaSetDevice(h->device));
+  Arena ar;
+  double* st;
+  ar.add(&st, 1);
+  MGW_TRY(ar.commit(h));
+  int* flag = reinterpret_cast<int*>(st);
+  MGW_CUDA(h, cudaMemsetAsync(flag, 0, sizeof(int), h->stream));
+  MGW_TRY(quantize(h, count, L, e, Lq, flag));
+  if (overflow_host) {
+    MGW_CUDA(h, cudaMemcpyAsync(overflow_host, flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    MGW_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (*overflow_host) return fail(h, MGW_ERR_ARG, "mgw_df_quantize: a value lies outside |L| < 2^(e-1), e = %d", e);
+  }
+  return MGW_OK;
 }

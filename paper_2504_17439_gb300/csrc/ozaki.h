@@ -541,6 +541,13 @@ mgw_status slice_gather_grid(mgw_handle* h, long rows, long K, const double* X, 
                              Sliced& out);
 // X' = X rounded to that grid (the FP64 values the two digits represent)
 mgw_status round_to_grid(mgw_handle* h, long n, const double* X, const int* gexp, double* Xr);
+// A tensor already on its grid as 16-bit integers q (value q 2^(e-16)):
+// slice a gather of it (two digits, exponent e for every row), read a gather
+// of its values, and quantize FP64 values into it (*overflow set when a value
+// lies outside the grid's range |x| < 2^(e-1))
+mgw_status slice_gather_q(mgw_handle* h, long rows, long K, const short* X, const Gather& g, int e, Sliced& out);
+mgw_status dequantize_gather(mgw_handle* h, long rows, long K, const short* X, const Gather& g, int e, double* out);
+mgw_status quantize(mgw_handle* h, long n, const double* L, int e, short* Lq, int* overflow);
 // 3D tensor map over digits: (k, row, digit), box (64, box_rows, 1)
 mgw_status digit_map(mgw_handle* h, CUtensorMap* map, const Sliced& s, int box_rows);
 
@@ -574,7 +581,8 @@ inline int best_split(long kept, long K, int sms) {
 }
 // C [M][N] (ldc) = A [M][K] (lda) B [K][N] (ldb), row-major, as an
 // FP64-accurate digit-sliced product (28 products); synchronises to read the
-// wait status
+// wait status.  Its digits live in slot buffers, so it may run inside a call
+// that holds workspace-arena pointers.
 mgw_status gemm_fp64_tc_nn(mgw_handle* h, int M, int N, int K, const double* A, long lda, const double* B, long ldb,
                            double* C, long ldc, const char* what);
 // sum of the split buffers: out[i] = (accumulate ? out[i] : 0) + sum_z part[z count + i]

@@ -229,14 +229,19 @@ __global__ void k_minmax(long n, const double* D, double* out) {
 
 using namespace mgw;
 
-extern "C" mgw_status mgw_response_moments(mgw_handle* h, const mgw_options* o, int nocc, int nvir, int naux,
-                                           int nmom, const double* eps_W, const double* Lov, double* Wmom) {
+// The response from the FP64 particle-hole block Lov, or (Lq != null: TDA,
+// MGW_MIXED) from the whole DF tensor on its grid as 16-bit integers with
+// exponent eq, V' being its particle-hole block.
+static mgw_status response_impl(mgw_handle* h, const mgw_options* o, int nocc, int nvir, int naux, int nmom,
+                                const double* eps_W, const double* Lov, const short* Lq, int eq, double* Wmom) {
   if (!h) return MGW_ERR_ARG;
   mgw_options def;
   mgw_options_default(&def);
   if (!o) o = &def;
-  if (nocc < 1 || nvir < 1 || naux < 1 || nmom < 1 || nmom > 64 || !eps_W || !Lov || !Wmom)
+  if (nocc < 1 || nvir < 1 || naux < 1 || nmom < 1 || nmom > 64 || !eps_W || (!Lov && !Lq) || !Wmom)
     return fail(h, MGW_ERR_ARG, "mgw_response_moments: bad sizes or null pointer");
+  if (Lq && (o->precision != MGW_MIXED || o->screening != MGW_TDA))
+    return fail(h, MGW_ERR_UNSUPPORTED, "mgw_response_moments_q: the 16-bit grid tensor is the MGW_MIXED TDA input");
   if (o->screening != MGW_TDA && o->screening != MGW_RPA)
     return fail(h, MGW_ERR_ARG, "mgw_response_moments: unknown screening %d", o->screening);
   if (o->screening == MGW_RPA && (o->nquad < 2 || o->nquad % 2))
@@ -305,7 +310,14 @@ extern "C" mgw_status mgw_response_moments(mgw_handle* h, const mgw_options* o, 
     oz::place_sliced(td, naux, ov, stt);
     oz::place_sliced(wd, naux, naux, sww);
     const oz::Gather gvt{ov + 1, 0, 1, naux + 1, 0, ov};  // V^T: rows ia, K = Q
-    if (mixed) {
+    if (Lq) {
+      // V' inside the whole tensor: element (Q, ia) at Lq[Q nmo^2 + i nmo + nocc + a]
+      const long nmo = nocc + nvir, n2 = nmo * nmo;
+      const short* Vq = Lq + nocc;
+      MGW_TRY(oz::slice_gather_q(h, naux, ov, Vq, oz::Gather{naux + 1L, 0, n2, nvir, nmo, 1}, eq, sv));
+      MGW_TRY(oz::slice_gather_q(h, ov, naux, Vq, oz::Gather{nvir, nmo, 1, naux + 1L, 0, n2}, eq, svt));
+      MGW_TRY(oz::dequantize_gather(h, naux, ov, Vq, oz::Gather{naux + 1L, 0, n2, nvir, nmo, 1}, eq, T0));
+    } else if (mixed) {
       int* gexp = reinterpret_cast<int*>(st + 2);
       MGW_TRY(oz::global_exponent(h, tsz, Lov, reinterpret_cast<unsigned long long*>(st + 1), gexp));
       MGW_TRY(oz::slice_rows_grid(h, naux, ov, Lov, ov, gexp, sv));
@@ -391,4 +403,21 @@ extern "C" mgw_status mgw_response_moments(mgw_handle* h, const mgw_options* o, 
   }
   if (rpa_tc && !h->defer_status) return tc::check_tc_status(h, P.dstatus, "mgw_response_moments");
   return MGW_OK;
+}
+
+extern "C" mgw_status mgw_response_moments(mgw_handle* h, const mgw_options* o, int nocc, int nvir, int naux,
+                                           int nmom, const double* eps_W, const double* Lov, double* Wmom) {
+  if (!Lov) return h ? fail(h, MGW_ERR_ARG, "mgw_response_moments: null Lov") : MGW_ERR_ARG;
+  return response_impl(h, o, nocc, nvir, naux, nmom, eps_W, Lov, nullptr, 0, Wmom);
+}
+
+extern "C" mgw_status mgw_response_moments_q(mgw_handle* h, const mgw_options* o, int nocc, int nvir, int naux,
+                                             int nmom, const double* eps_W, const short* Lq, int e, double* Wmom) {
+  if (!Lq) return h ? fail(h, MGW_ERR_ARG, "mgw_response_moments_q: null Lq") : MGW_ERR_ARG;
+  mgw_options m;
+  if (o) m = *o;
+  else mgw_options_default(&m);
+  m.precision = MGW_MIXED;
+  m.screening = MGW_TDA;
+  return response_impl(h, &m, nocc, nvir, naux, nmom, eps_W, nullptr, Lq, e, Wmom);
 }

@@ -115,16 +115,23 @@ __global__ void k_reduce_splits(long count, int nsplit, const double* part, doub
 
 using namespace mgw;
 
-extern "C" mgw_status mgw_sigma_moments(mgw_handle* h, const mgw_options* o, int nocc, int nvir, int naux,
-                                        int nmom, const double* eps_G, const double* L, const double* Wmom,
-                                        double* sig_hole, double* sig_part) {
+// The Sigma build over Green's-function indices x = 0..nxs-1 (the first
+// nhole of them holes), with L [naux][nxs][nmo] (row x of slab P is
+// L_{P,x q}; for the orbitals themselves nxs = nmo and the slabs are
+// symmetric), from the FP64 tensor L, or (Lq != null, MGW_MIXED only) from
+// the tensor already on its grid as 16-bit integers with exponent eq.
+static mgw_status sigma_impl(mgw_handle* h, const mgw_options* o, int nmo, int nxs, int nhole, int naux, int nmom,
+                             const double* eps_G, const double* L, const short* Lq, int eq, const double* Wmom,
+                             double* sig_hole, double* sig_part) {
   if (!h) return MGW_ERR_ARG;
   mgw_options def;
   mgw_options_default(&def);
   if (!o) o = &def;
-  if (nocc < 1 || nvir < 1 || naux < 1 || nmom < 1 || nmom > kMaxMom || !eps_G || !L || !Wmom || !sig_hole ||
-      !sig_part)
+  if (nmo < 1 || nxs < 1 || nhole < 0 || nhole > nxs || naux < 1 || nmom < 1 || nmom > kMaxMom || !eps_G ||
+      (!L && !Lq) || !Wmom || !sig_hole || !sig_part)
     return fail(h, MGW_ERR_ARG, "mgw_sigma_moments: bad sizes or null pointer");
+  if (Lq && o->precision != MGW_MIXED)
+    return fail(h, MGW_ERR_UNSUPPORTED, "mgw_sigma_moments_q: the 16-bit grid tensor is the MGW_MIXED input");
   if (o->precision != MGW_FP64 && o->precision != MGW_FP64_TC && o->precision != MGW_MIXED)
     return fail(h, MGW_ERR_UNSUPPORTED, "mgw_sigma_moments: precision %d not built", o->precision);
   // MGW_MIXED: L enters both products as the same tensor L' (L rounded to one
@@ -133,7 +140,7 @@ extern "C" mgw_status mgw_sigma_moments(mgw_handle* h, const mgw_options* o, int
   const bool tc = o->precision == MGW_FP64_TC || mixed;
   const int lns = mixed ? oz::kGridSlices : oz::kSlices;
   MGW_CUDA(h, cudaSetDevice(h->device));
-  const int nmo = nocc + nvir;
+  const long sx = (long)nxs * nmo;  // slab stride of L
   constexpr int BM = 96, BN = 64;
   const int PB = std::max(1, BM / nmom);
   const long ngroups = (naux + PB - 1) / PB;
@@ -141,7 +148,7 @@ extern "C" mgw_status mgw_sigma_moments(mgw_handle* h, const mgw_options* o, int
   // chunk of x per pass: Z holds nmom * naux * xc * nmo doubles (~1 GiB budget)
   const double per_x = (double)nmom * naux * nmo * sizeof(double);
   int xc = o->xchunk > 0 ? o->xchunk : (int)std::max(1.0, std::floor((1024.0 * 1024 * 1024) / per_x));
-  xc = std::min(xc, nmo);
+  xc = std::min(xc, nxs);
 
   // GEMM2 (symmetric output, upper tiles) is split along K until the launch
   // has enough CTAs to fill the GPU several times over
@@ -179,14 +186,14 @@ extern "C" mgw_status mgw_sigma_moments(mgw_handle* h, const mgw_options* o, int
     oz::place_sliced(wdig, ngroups_t * 128, naux, sw);
     MGW_TRY(oz::slice_grouped(h, nmom, PBt, naux, Wmom, sw));
     MGW_TRY(oz::digit_map(h, &mw, sw, oz::BM));
-    if (mixed)
-      MGW_TRY(oz::global_exponent(h, (long)naux * nmo * nmo, L, reinterpret_cast<unsigned long long*>(st + 1),
+    if (mixed && !Lq)
+      MGW_TRY(oz::global_exponent(h, (long)naux * sx, L, reinterpret_cast<unsigned long long*>(st + 1),
                                   reinterpret_cast<int*>(st + 2)));
   }
   const int* gexp = tc ? reinterpret_cast<const int*>(st + 2) : nullptr;
 
   for (int sector = 0; sector < 2; ++sector) {
-    const int xbeg = sector == 0 ? 0 : nocc, xend = sector == 0 ? nocc : nmo;
+    const int xbeg = sector == 0 ? 0 : nhole, xend = sector == 0 ? nhole : nxs;
     const double sgn = sector == 0 ? -1.0 : 1.0;
     double* sig = sector == 0 ? sig_hole : sig_part;
     BinomCoef bc;
@@ -197,11 +204,13 @@ extern "C" mgw_status mgw_sigma_moments(mgw_handle* h, const mgw_options* o, int
       const long ncol = (long)nx * nmo;
       if (tc) {
         oz::place_sliced(ldig, ncol, naux, sl, lns);
-        if (mixed)
-          MGW_TRY(oz::slice_gather_grid(h, ncol, naux, L + (long)x0 * nmo,
-                                        oz::Gather{ncol + 1, 0, 1, naux + 1L, 0, (long)nmo * nmo}, gexp, sl));
+        const oz::Gather gy{ncol + 1, 0, 1, naux + 1L, 0, sx};  // rows (x, q), K = P
+        if (Lq)
+          MGW_TRY(oz::slice_gather_q(h, ncol, naux, Lq + (long)x0 * nmo, gy, eq, sl));
+        else if (mixed)
+          MGW_TRY(oz::slice_gather_grid(h, ncol, naux, L + (long)x0 * nmo, gy, gexp, sl));
         else
-          MGW_TRY(oz::slice_cols(h, ncol, naux, L + (long)x0 * nmo, (long)nmo * nmo, sl));
+          MGW_TRY(oz::slice_cols(h, ncol, naux, L + (long)x0 * nmo, sx, sl));
         CUtensorMap ml;
         MGW_TRY(oz::digit_map(h, &ml, sl, oz::BN));
         auto launch_y = [&](auto epi) {
@@ -220,7 +229,7 @@ extern "C" mgw_status mgw_sigma_moments(mgw_handle* h, const mgw_options* o, int
       } else {
         EpiBinomialT<BinomCoef> epi{Z, eps_G + x0, nmom, PB, naux, nmo, ncol, bc};
         AGroupedMoments A{Wmom, nmom, PB, naux, BM};
-        BRowMajor B{L + (long)x0 * nmo, (long)nmo * nmo, 0};
+        BRowMajor B{L + (long)x0 * nmo, sx, 0};
         MGW_TRY((dgemm<BM, BN>(h, ngroups * BM, ncol, naux, 1, A, B, epi, "sigma_y_binomial")));
       }
       // Sigma(n) (+)= sum_{P,x} L[P][x][p] Z(n)[(P,x)][q]
@@ -230,8 +239,10 @@ extern "C" mgw_status mgw_sigma_moments(mgw_handle* h, const mgw_options* o, int
         oz::Sliced sa2, sz2;
         oz::place_sliced(adig, nmo, K2, sa2, lns);
         oz::place_sliced(zdig, (long)nmom * nmo, K2, sz2);
-        const oz::Gather ga2{nmo + 1L, 0, 1, naux, nmo, (long)nmo * nmo};
-        if (mixed)
+        const oz::Gather ga2{nmo + 1L, 0, 1, naux, nmo, sx};
+        if (Lq)
+          MGW_TRY(oz::slice_gather_q(h, nmo, K2, Lq + (long)x0 * nmo, ga2, eq, sa2));
+        else if (mixed)
           MGW_TRY(oz::slice_gather_grid(h, nmo, K2, L + (long)x0 * nmo, ga2, gexp, sa2));
         else
           MGW_TRY(oz::slice_gather(h, nmo, K2, L + (long)x0 * nmo, ga2, sa2));
@@ -264,7 +275,7 @@ extern "C" mgw_status mgw_sigma_moments(mgw_handle* h, const mgw_options* o, int
         first = false;
         continue;
       }
-      AKMajor2 A2{L + (long)x0 * nmo, nx, (long)nmo * nmo, nmo, 0};
+      AKMajor2 A2{L + (long)x0 * nmo, nx, sx, nmo, 0};
       BRowMajor B2{Z, nmo, (long)naux * ncol};
       const long K2 = (long)naux * nx;
       const int ns = (int)std::min<long>(nsplit, std::max(1L, K2 / 256));
@@ -288,4 +299,33 @@ extern "C" mgw_status mgw_sigma_moments(mgw_handle* h, const mgw_options* o, int
   }
   if (tc && !h->defer_status) return tc::check_tc_status(h, dstatus, "mgw_sigma_moments");
   return MGW_OK;
+}
+
+extern "C" mgw_status mgw_sigma_moments(mgw_handle* h, const mgw_options* o, int nocc, int nvir, int naux,
+                                        int nmom, const double* eps_G, const double* L, const double* Wmom,
+                                        double* sig_hole, double* sig_part) {
+  if (!L) return h ? fail(h, MGW_ERR_ARG, "mgw_sigma_moments: null L") : MGW_ERR_ARG;
+  if (nocc < 1 || nvir < 1) return h ? fail(h, MGW_ERR_ARG, "mgw_sigma_moments: bad sizes") : MGW_ERR_ARG;
+  return sigma_impl(h, o, nocc + nvir, nocc + nvir, nocc, naux, nmom, eps_G, L, nullptr, 0, Wmom, sig_hole,
+                    sig_part);
+}
+
+extern "C" mgw_status mgw_sigma_moments_x(mgw_handle* h, const mgw_options* o, int nmo, int nx, int nhole, int naux,
+                                          int nmom, const double* eps_x, const double* Lx, const double* Wmom,
+                                          double* sig_hole, double* sig_part) {
+  if (!Lx) return h ? fail(h, MGW_ERR_ARG, "mgw_sigma_moments_x: null Lx") : MGW_ERR_ARG;
+  return sigma_impl(h, o, nmo, nx, nhole, naux, nmom, eps_x, Lx, nullptr, 0, Wmom, sig_hole, sig_part);
+}
+
+extern "C" mgw_status mgw_sigma_moments_q(mgw_handle* h, const mgw_options* o, int nocc, int nvir, int naux,
+                                          int nmom, const double* eps_G, const short* Lq, int e,
+                                          const double* Wmom, double* sig_hole, double* sig_part) {
+  if (!Lq) return h ? fail(h, MGW_ERR_ARG, "mgw_sigma_moments_q: null Lq") : MGW_ERR_ARG;
+  mgw_options m;
+  if (o) m = *o;
+  else mgw_options_default(&m);
+  m.precision = MGW_MIXED;
+  if (nocc < 1 || nvir < 1) return h ? fail(h, MGW_ERR_ARG, "mgw_sigma_moments_q: bad sizes") : MGW_ERR_ARG;
+  return sigma_impl(h, &m, nocc + nvir, nocc + nvir, nocc, naux, nmom, eps_G, nullptr, Lq, e, Wmom, sig_hole,
+                    sig_part);
 }

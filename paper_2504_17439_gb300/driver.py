@@ -121,6 +121,46 @@ def fsgw(h: mgw.Handle, hcore: torch.Tensor, L: torch.Tensor, eps: torch.Tensor,
     return dict(eps_qp=eps_qp, F=F, zeta=st.zeta, mu=st.mu, converged=False, history=hist)
 
 
+def scgw(h: mgw.Handle, eps: torch.Tensor, L: torch.Tensor, nocc: int, nmom_max: int,
+         screening: int = mgw.MGW_TDA, g0: bool = False, w0: bool = False, conv: float = 1e-6,
+         max_iter: int = 40, opts: mgw.Options | None = None) -> dict:
+    """scGW, GW0 (w0) and G0W (g0), Algorithm 5 (readings S1-S3): each
+    iteration builds the response moments over the current (i, a) space, the
+    self-energy moments over the current Green's-function space, both chains
+    and H~ (f + Sigma_inf = diag(eps)); then (unless g0) G moves to the QMOs
+    of H~ with eps^G = E, and (unless w0) the (i, a) space to occupied x
+    virtual QMOs with eps^W = E, until the QP energies change by less than
+    conv."""
+    o = opts if opts is not None else mgw.options()
+    o.screening = screening
+    naux, nmo = L.shape[0], L.shape[1]
+    nmom, nblk = 2 * nmom_max + 2, nmom_max + 1
+    fock = torch.diag(eps).contiguous()
+    epsG, epsW, mG, mW = eps.clone(), eps.clone(), nocc, nocc
+    Lx = L.contiguous()                        # x-major: the orbitals' slabs are symmetric
+    Via = h.mgw_extract_ov(nocc, nmo - nocc, L)
+    prev, hist = None, []
+    for it in range(max_iter):
+        nxW = epsW.shape[0]
+        W = h.mgw_response_moments(o, mW, nxW - mW, naux, nmom, epsW, Via.contiguous())
+        sh, sp = h.mgw_sigma_moments_x(o, nmo, epsG.shape[0], mG, naux, nmom, epsG.contiguous(), Lx, W)
+        ch, ah, bh, rh = h.mgw_block_lanczos(o, nmo, nmom, sh)
+        cp, ap, bp, rp = h.mgw_block_lanczos(o, nmo, nmom, sp)
+        qp = h.mgw_qp_solve(o, nmo, nblk, rh, rp, fock, (ch, ah, bh), (cp, ap, bp), 0.0, 2.0 * nocc,
+                            want_chi=True)
+        d = float((qp["eps_qp"] - prev).abs().max()) if prev is not None else float("inf")
+        hist.append(dict(iteration=it, dqp=d, poles=qp["E"].shape[0], nelec=qp["nelec"]))
+        prev = qp["eps_qp"]
+        if d < conv:
+            return dict(qp, converged=True, history=hist)
+        Lt, Vq = h.mgw_qmo_tensors(L, qp["chi"].contiguous(), qp["m"])
+        if not g0:
+            epsG, mG, Lx = qp["E"], qp["m"], Lt
+        if not w0:
+            epsW, mW, Via = qp["E"], qp["m"], Vq
+    return dict(qp, converged=False, history=hist)
+
+
 def qsgw(h: mgw.Handle, hcore: torch.Tensor, L: torch.Tensor, eps: torch.Tensor, nocc: int, nmom_max: int,
          reg: str = "srg", delta: float = 1e-3, srg_s: float = 100.0, screening: int = mgw.MGW_TDA,
          opts: mgw.Options | None = None, conv: float = 1e-8, max_outer: int = 60, diis_space: int = 8,

@@ -103,6 +103,12 @@ _SIGS = {
     "mgw_gemm_fp64_emu": [_I, _I, _I, _P, _P, _P],
     "mgw_selftest_bounded_wait": [_D],
     "mgw_gemm_mixed": [_I, _I, _I, _P, _P, _P],
+    "mgw_sigma_moments_x": [_P, _I, _I, _I, _I, _I, _P, _P, _P, _P, _P],
+    "mgw_qmo_tensors": [_I, _I, _I, _I, _P, _P, _P, _P],
+    "mgw_df_absmax": [ctypes.c_long, _P, ctypes.POINTER(_D)],
+    "mgw_df_quantize": [ctypes.c_long, _P, _I, _P, ctypes.POINTER(_I)],
+    "mgw_response_moments_q": [_P, _I, _I, _I, _I, _P, _P, _I, _P],
+    "mgw_sigma_moments_q": [_P, _I, _I, _I, _I, _P, _P, _I, _P, _P, _P],
     "mgw_response_moments": [_P, _I, _I, _I, _I, _P, _P, _P],
     "mgw_sigma_moments": [_P, _I, _I, _I, _I, _P, _P, _P, _P, _P],
     "mgw_block_lanczos": [_P, _I, _I, _P, _P, _P, _P, ctypes.POINTER(_I)],
@@ -155,6 +161,8 @@ def load(path: str | None = None):
     lib.mgw_sigma_moments_batched.restype = _I
     lib.mgw_fsgw_step.argtypes = [_P, _P, ctypes.POINTER(FsgwState)]
     lib.mgw_fsgw_step.restype = _I
+    lib.mgw_grid_exponent.argtypes = [_D]
+    lib.mgw_grid_exponent.restype = _I
     lib.mgw_qsgw_step.argtypes = [_P, _P, ctypes.POINTER(QsgwState)]
     lib.mgw_qsgw_step.restype = _I
     lib.mgw_hf_core.argtypes = [_P, _I, _I, _I, _P, _P, _P]
@@ -412,6 +420,70 @@ class Handle:
         self._check(self._lib.mgw_gemm_mixed(self._h, M, N, K, _ptr(A, (M, K), "A"), _ptr(B, (N, K), "B"),
                                              _ptr(C, (M, N), "C")))
         return C
+
+    def mgw_sigma_moments_x(self, opts: Options, nmo, nx, nhole, naux, nmom, eps_x, Lx, Wmom):
+        dev = eps_x.device
+        sh = torch.empty((nmom, nmo, nmo), dtype=torch.float64, device=dev)
+        sp = torch.empty_like(sh)
+        self._check(self._lib.mgw_sigma_moments_x(self._h, ctypes.byref(opts), nmo, nx, nhole, naux, nmom,
+                                                  _ptr(eps_x, (nx,), "eps_x"), _ptr(Lx, (naux, nx, nmo), "Lx"),
+                                                  _ptr(Wmom, (nmom, naux, naux), "Wmom"), _ptr(sh), _ptr(sp)))
+        return sh, sp
+
+    def mgw_qmo_tensors(self, L, chi, m):
+        """(Lt [naux][nx][nmo], Via [naux][m * (nx - m)] or None) for the QMOs of chi [nmo][nx]."""
+        naux, nmo = L.shape[0], L.shape[1]
+        nx = chi.shape[1]
+        Lt = torch.empty((naux, nx, nmo), dtype=torch.float64, device=L.device)
+        Via = torch.empty((naux, m * (nx - m)), dtype=torch.float64, device=L.device) if 0 < m < nx else None
+        self._check(self._lib.mgw_qmo_tensors(self._h, nmo, naux, nx, m, _ptr(L, (naux, nmo, nmo), "L"),
+                                              _ptr(chi, (nmo, nx), "chi"), _ptr(Lt), _ptr(Via)))
+        return Lt, Via
+
+    def mgw_df_absmax(self, L):
+        out = ctypes.c_double()
+        self._check(self._lib.mgw_df_absmax(self._h, L.numel(), _ptr(L), ctypes.byref(out)))
+        return out.value
+
+    def mgw_grid_exponent(self, absmax):
+        return int(self._lib.mgw_grid_exponent(float(absmax)))
+
+    def mgw_df_quantize(self, L, e, Lq=None):
+        """Lq (int16, same shape) = round(L 2^(16-e)); raises on values outside the grid's range."""
+        if L.dtype != torch.float64:
+            raise ValueError("L must be float64")
+        Lq = Lq if Lq is not None else torch.empty(L.shape, dtype=torch.int16, device=L.device)
+        if Lq.dtype != torch.int16 or Lq.numel() != L.numel() or not Lq.is_contiguous():
+            raise ValueError("Lq must be a contiguous int16 tensor of L's size")
+        ov = ctypes.c_int()
+        self._check(self._lib.mgw_df_quantize(self._h, L.numel(), _ptr(L), int(e), Lq.data_ptr(), ctypes.byref(ov)))
+        return Lq
+
+    def _qptr(self, Lq, shape):
+        if not Lq.is_cuda or Lq.dtype != torch.int16 or not Lq.is_contiguous() or tuple(Lq.shape) != tuple(shape):
+            raise ValueError(f"Lq must be a contiguous int16 CUDA tensor of shape {shape}")
+        return Lq.data_ptr()
+
+    def mgw_response_moments_q(self, opts: Options, nocc, nvir, naux, nmom, eps_W, Lq, e, Wmom=None):
+        nmo = nocc + nvir
+        Wmom = Wmom if Wmom is not None else torch.empty((nmom, naux, naux), dtype=torch.float64, device=eps_W.device)
+        self._check(self._lib.mgw_response_moments_q(self._h, ctypes.byref(opts), nocc, nvir, naux, nmom,
+                                                     _ptr(eps_W, (nmo,), "eps_W"), self._qptr(Lq, (naux, nmo, nmo)),
+                                                     int(e), _ptr(Wmom, (nmom, naux, naux), "Wmom")))
+        return Wmom
+
+    def mgw_sigma_moments_q(self, opts: Options, nocc, nvir, naux, nmom, eps_G, Lq, e, Wmom, sig_hole=None,
+                            sig_part=None):
+        nmo = nocc + nvir
+        dev = eps_G.device
+        sh = sig_hole if sig_hole is not None else torch.empty((nmom, nmo, nmo), dtype=torch.float64, device=dev)
+        sp = sig_part if sig_part is not None else torch.empty((nmom, nmo, nmo), dtype=torch.float64, device=dev)
+        self._check(self._lib.mgw_sigma_moments_q(self._h, ctypes.byref(opts), nocc, nvir, naux, nmom,
+                                                  _ptr(eps_G, (nmo,), "eps_G"), self._qptr(Lq, (naux, nmo, nmo)),
+                                                  int(e), _ptr(Wmom, (nmom, naux, naux), "Wmom"),
+                                                  _ptr(sh, (nmom, nmo, nmo), "sig_hole"),
+                                                  _ptr(sp, (nmom, nmo, nmo), "sig_part")))
+        return sh, sp
 
     def mgw_selftest_bounded_wait(self, limit_s):
         """A bounded wait that nothing satisfies: raises MgwError(MGW_ERR_TIMEOUT)."""
