@@ -59,6 +59,9 @@ WORKLOADS = {
     "g0w0-nmo400-naux1600": dict(shape=Shape(60, 340, 1600, 7), seed=SEED_BASE + 100),
     # mid-size system for profiler captures: inputs above L2, a few GB on device
     "g0w0-nmo200-naux800": dict(shape=Shape(30, 170, 800, 7), seed=SEED_BASE + 300),
+    # profiler captures of the headline's contraction length (K = naux = 4800)
+    # on a few GB of device memory
+    "g0w0-nmo200-naux4800": dict(shape=Shape(30, 170, 4800, 7), seed=SEED_BASE + 310),
     # pigment-molecule scale, mixed-precision workload
     "g0w0-nmo1200-naux4800": dict(shape=Shape(240, 960, 4800, 7), seed=SEED_BASE + 200),
     # chlorophyll-A scale (2147 orbitals, 482 electrons, naux = 4 nmo): 317 GB

@@ -252,8 +252,16 @@ mgw_status eig_physical_rows(mgw_handle* h, int n, int nrows, double* H, double*
   // 1. H = Q T Q^T (lower storage; H is symmetric, row- and column-major alike)
   int lwork = 0, lw2 = 0;
   MGW_SOLVER(h, cusolverDnDsytrd_bufferSize(h->solver, CUBLAS_FILL_MODE_LOWER, n, H, n, d, e, tau, &lwork));
-  MGW_SOLVER(h, cusolverDnDormtr_bufferSize(h->solver, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, n,
-                                            nrows, H, n, tau, P, n, &lw2));
+  // ormtr takes the unit columns in blocks (the 32-bit solver API refuses
+  // large n x nrows operands: at n = 36 499 it rejects 2147 columns at once)
+  int cw = std::max(1, std::min(nrows, (int)std::max(1L, (1L << 25) / n)));
+  while (true) {
+    const cusolverStatus_t q = cusolverDnDormtr_bufferSize(h->solver, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER,
+                                                           CUBLAS_OP_T, n, cw, H, n, tau, P, n, &lw2);
+    if (q == CUSOLVER_STATUS_SUCCESS) break;
+    if (cw == 1) return fail(h, MGW_ERR_CUDA, "ormtr_bufferSize: cusolver status %d at n = %d", (int)q, n);
+    cw = std::max(1, cw / 2);
+  }
   lwork = std::max(std::max(lwork, lw2), 1);
   double* work;
   MGW_TRY(slot_buffer(h, 82, (size_t)lwork, &work));
@@ -262,8 +270,10 @@ mgw_status eig_physical_rows(mgw_handle* h, int n, int nrows, double* H, double*
   k_unit_columns<<<cdiv((long)n * nrows, 256) > 152u * 16 ? 152u * 16 : cdiv((long)n * nrows, 256), 256, 0,
                    h->stream>>>(n, nrows, P);
   MGW_TRY(check_launch(h, "unit_columns"));
-  MGW_SOLVER(h, cusolverDnDormtr(h->solver, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, n, nrows, H, n,
-                                 tau, P, n, work, lwork, h->dinfo));
+  for (int c0 = 0; c0 < nrows; c0 += cw)
+    MGW_SOLVER(h, cusolverDnDormtr(h->solver, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, n,
+                                   std::min(cw, nrows - c0), H, n, tau, P + (long)c0 * n, n, work, lwork,
+                                   h->dinfo));
   // 2. eigenvalues of T
   k_tri_bounds<<<1, 256, 0, h->stream>>>(n, d, e, bounds);
   k_square<<<cdiv(n, 256), 256, 0, h->stream>>>(n - 1, e, e2);
