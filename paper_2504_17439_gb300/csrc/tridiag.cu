@@ -19,6 +19,11 @@
 // A full eigen-decomposition (syevd) does 1. plus a divide-and-conquer
 // tridiagonal solve with every eigenvector and the back-transformation of
 // all of them; here only nrows of n rows are ever formed.
+//
+// The 32-bit dense solver API takes matrices of up to 2^31 bytes: ormtr
+// refused n = 36 499 (cusolver status 3, invalid value, for any number of
+// columns).  Beyond that size the 64-bit syevd (Xsyevd) runs instead, with
+// every eigenvector, and its first nrows rows are copied out.
 #include "mgw_internal.h"
 #include "ozaki.h"
 
@@ -228,8 +233,56 @@ __global__ void k_unit_columns(int n, int nrows, double* C) {
   }
 }
 
+// chi[p][a] = V[a n + p] for p < nrows: the first rows of column-major
+// eigenvectors, through a 32 x 32 shared-memory tile
+__global__ void k_rows_of_columns(int n, int nrows, const double* __restrict__ V, double* __restrict__ chi,
+                                  long ldchi) {
+  __shared__ double t[32][33];
+  const long a0 = (long)blockIdx.x * 32, p0 = (long)blockIdx.y * 32;
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {  // read down a column (p fastest)
+    const long a = a0 + j, p = p0 + threadIdx.x;
+    t[j][threadIdx.x] = (a < n && p < nrows) ? V[a * n + p] : 0.0;
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {  // write along a row (a fastest)
+    const long p = p0 + j, a = a0 + threadIdx.x;
+    if (p < nrows && a < n) chi[p * ldchi + a] = t[threadIdx.x][j];
+  }
+}
+
+static mgw_status eig_dense_64(mgw_handle* h, int n, int nrows, double* H, double* E, double* chi, long ldchi) {
+  ProfSpan span(h, "syevd_64");
+  cusolverDnParams_t params = nullptr;
+  MGW_SOLVER(h, cusolverDnCreateParams(&params));
+  size_t dbytes = 0, hbytes = 0;
+  cusolverStatus_t s = cusolverDnXsyevd_bufferSize(h->solver, params, CUSOLVER_EIG_MODE_VECTOR,
+                                                   CUBLAS_FILL_MODE_LOWER, n, CUDA_R_64F, H, n, CUDA_R_64F, E,
+                                                   CUDA_R_64F, &dbytes, &hbytes);
+  void* dwork = nullptr;
+  std::vector<char> hwork(std::max<size_t>(hbytes, 1));
+  if (s == CUSOLVER_STATUS_SUCCESS) {
+    const cudaError_t ce = cudaMallocAsync(&dwork, std::max<size_t>(dbytes, 16), h->stream);
+    if (ce != cudaSuccess) {
+      cusolverDnDestroyParams(params);
+      return fail(h, MGW_ERR_NOMEM, "syevd_64: %zu bytes of workspace: %s", dbytes, cudaGetErrorString(ce));
+    }
+    s = cusolverDnXsyevd(h->solver, params, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, CUDA_R_64F, H, n,
+                         CUDA_R_64F, E, CUDA_R_64F, dwork, dbytes, hwork.data(), hbytes, h->dinfo);
+    cudaFreeAsync(dwork, h->stream);
+  }
+  cusolverDnDestroyParams(params);
+  if (s != CUSOLVER_STATUS_SUCCESS) return fail(h, MGW_ERR_CUDA, "syevd_64: cusolver status %d (n = %d)", (int)s, n);
+  int info = 0;
+  MGW_CUDA(h, cudaMemcpyAsync(&info, h->dinfo, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  MGW_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (info != 0) return fail(h, MGW_ERR_NO_CONV, "syevd_64: info = %d (n = %d)", info, n);
+  k_rows_of_columns<<<dim3(cdiv(n, 32), cdiv(nrows, 32)), dim3(32, 8), 0, h->stream>>>(n, nrows, H, chi, ldchi);
+  return check_launch(h, "rows_of_columns");
+}
+
 mgw_status eig_physical_rows(mgw_handle* h, int n, int nrows, double* H, double* E, double* chi, long ldchi) {
   if (n <= 0) return MGW_OK;
+  if ((long)n * n > (1L << 31) / (long)sizeof(double)) return eig_dense_64(h, n, nrows, H, E, chi, ldchi);
   const long n2 = (long)n * n;
   const int nb = std::min(n, 4096);  // eigenvectors per inverse-iteration batch
   double *d, *e, *e2, *tau, *bounds, *P, *Z, *U0, *U1, *U2, *ML;
@@ -252,16 +305,8 @@ mgw_status eig_physical_rows(mgw_handle* h, int n, int nrows, double* H, double*
   // 1. H = Q T Q^T (lower storage; H is symmetric, row- and column-major alike)
   int lwork = 0, lw2 = 0;
   MGW_SOLVER(h, cusolverDnDsytrd_bufferSize(h->solver, CUBLAS_FILL_MODE_LOWER, n, H, n, d, e, tau, &lwork));
-  // ormtr takes the unit columns in blocks (the 32-bit solver API refuses
-  // large n x nrows operands: at n = 36 499 it rejects 2147 columns at once)
-  int cw = std::max(1, std::min(nrows, (int)std::max(1L, (1L << 25) / n)));
-  while (true) {
-    const cusolverStatus_t q = cusolverDnDormtr_bufferSize(h->solver, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER,
-                                                           CUBLAS_OP_T, n, cw, H, n, tau, P, n, &lw2);
-    if (q == CUSOLVER_STATUS_SUCCESS) break;
-    if (cw == 1) return fail(h, MGW_ERR_CUDA, "ormtr_bufferSize: cusolver status %d at n = %d", (int)q, n);
-    cw = std::max(1, cw / 2);
-  }
+  MGW_SOLVER(h, cusolverDnDormtr_bufferSize(h->solver, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, n,
+                                            nrows, H, n, tau, P, n, &lw2));
   lwork = std::max(std::max(lwork, lw2), 1);
   double* work;
   MGW_TRY(slot_buffer(h, 82, (size_t)lwork, &work));
@@ -270,10 +315,8 @@ mgw_status eig_physical_rows(mgw_handle* h, int n, int nrows, double* H, double*
   k_unit_columns<<<cdiv((long)n * nrows, 256) > 152u * 16 ? 152u * 16 : cdiv((long)n * nrows, 256), 256, 0,
                    h->stream>>>(n, nrows, P);
   MGW_TRY(check_launch(h, "unit_columns"));
-  for (int c0 = 0; c0 < nrows; c0 += cw)
-    MGW_SOLVER(h, cusolverDnDormtr(h->solver, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, n,
-                                   std::min(cw, nrows - c0), H, n, tau, P + (long)c0 * n, n, work, lwork,
-                                   h->dinfo));
+  MGW_SOLVER(h, cusolverDnDormtr(h->solver, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, n, nrows, H, n,
+                                 tau, P, n, work, lwork, h->dinfo));
   // 2. eigenvalues of T
   k_tri_bounds<<<1, 256, 0, h->stream>>>(n, d, e, bounds);
   k_square<<<cdiv(n, 256), 256, 0, h->stream>>>(n - 1, e, e2);

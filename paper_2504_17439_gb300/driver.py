@@ -13,9 +13,18 @@ from . import mgw
 
 def g0w0(h: mgw.Handle, eps_G: torch.Tensor, L: torch.Tensor, nocc: int, nmom_max: int,
          screening: int = mgw.MGW_TDA, eps_W: torch.Tensor | None = None, fock: torch.Tensor | None = None,
-         opts: mgw.Options | None = None, Lov: torch.Tensor | None = None, want_chi: bool = False) -> dict:
+         opts: mgw.Options | None = None, Lov: torch.Tensor | None = None, want_chi: bool = False,
+         naf_eps: float | None = None, naf_all_pairs: bool = False) -> dict:
     """Response moments -> W -> Sigma(n,<), Sigma(n,>) -> block Lanczos per
-    sector -> H~ eigensolve, QP energies, Aufbau.  All tensors on the GPU."""
+    sector -> H~ eigensolve, QP energies, Aufbau.  All tensors on the GPU.
+    With naf_eps, L is first compressed to its natural auxiliary functions
+    (Sec. II D, Eq. 14: eigenvalues of the pair metric above naf_eps) and
+    every later step runs on n_naf instead of naux auxiliary functions."""
+    n_naf = None
+    if naf_eps is not None:
+        L, _ = h.mgw_naf_compress(nocc, L, naf_eps, naf_all_pairs)
+        n_naf = L.shape[0]
+        Lov = None
     naux, nmo = L.shape[0], L.shape[1]
     nvir = nmo - nocc
     nmom = 2 * nmom_max + 2
@@ -31,7 +40,8 @@ def g0w0(h: mgw.Handle, eps_G: torch.Tensor, L: torch.Tensor, nocc: int, nmom_ma
     f = torch.diag(eps_G) if fock is None else fock
     qp = h.mgw_qp_solve(o, nmo, nblk, rh, rp, f.contiguous(), (ch, ah, bh), (cp, ap, bp), 0.0, 2.0 * nocc,
                         want_chi=want_chi)
-    return dict(W=Wmom, sigma_hole=sh, sigma_part=sp, hole=(ch, ah, bh, rh), part=(cp, ap, bp, rp), **qp)
+    return dict(W=Wmom, sigma_hole=sh, sigma_part=sp, hole=(ch, ah, bh, rh), part=(cp, ap, bp, rp), n_naf=n_naf,
+                **qp)
 
 
 def evgw(h: mgw.Handle, eps: torch.Tensor, L: torch.Tensor, nocc: int, nmom_max: int,

@@ -82,3 +82,26 @@ def test_spectral_function_rejects_a_non_positive_broadening(h):
     E = torch.zeros(3, dtype=torch.float64, device="cuda")
     with pytest.raises(mgw.MgwError):
         h.mgw_spectral_function(E, E, E, 0.0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp64_tc", "mixed"])
+def test_g0w0_on_natural_auxiliary_functions(h, precision):
+    """The driver compresses L to its natural auxiliary functions (Eq. 14)
+    and runs the whole chain on n_naf of them: QP energies as the oracle's
+    chain on the oracle's compressed tensor (the rows' signs and the basis
+    inside the NAF space do not enter the moments, which are bilinear in L).
+    The mixed precision is held to 1 meV of that FP64 oracle."""
+    from paper_2504_17439_gb300 import driver, mgw
+
+    shape, seed = mgw_inputs.workload("g0w0-nmo24-naux72")
+    eps, L = mgw_inputs.system(shape, seed)
+    _, lam = orc.naf_basis(L, shape.nocc, -1.0, "no_vv")
+    keep = (2 * L.shape[0]) // 3
+    thresh = 0.5 * (lam[keep - 1] + lam[keep])
+    ref = orc.g0w0(eps, orc.naf_compress(L, shape.nocc, thresh, "no_vv"), shape.nocc, shape.nmom_max)
+    prec = {"fp64": mgw.MGW_FP64, "fp64_tc": mgw.MGW_FP64_TC, "mixed": mgw.MGW_MIXED}[precision]
+    r = driver.g0w0(h, torch.from_numpy(eps).cuda(), torch.from_numpy(L).cuda(), shape.nocc, shape.nmom_max,
+                    opts=mgw.options(precision=prec), naf_eps=thresh)
+    assert r["n_naf"] == keep
+    err = np.abs(r["eps_qp"].cpu().numpy() - ref["eps_qp"]).max()
+    assert err < (3.6749e-5 if precision == "mixed" else 1e-8), err
