@@ -57,7 +57,9 @@ typedef enum { MGW_TDA = 0, MGW_RPA = 1 } mgw_screening;
  * L (and V for the TDA response) rounded to a multiple of 2^(e-16) where
  * max |L| < 2^(e-1), i.e. to 16 bits of the largest element, and carried as
  * two BF16 digits; the moment-carrying operands (eta~, W, Z) keep seven
- * digits and every digit product is exact, 13 BF16 products per product.
+ * digits, 13 BF16 products per product, each exact, their sums exact down to
+ * 2^-40 of the top and in FP32 below.  Its contractions need naux <= 65536
+ * (K per launch of the tensor-core kernel; longer K elsewhere is split).
  * The results are the FP64-accurate moments of the system with the rounded
  * tensor, a consistent moment sequence (no amplification by the block
  * Lanczos step): QP energies move by a few 1e-5 to 1e-4 meV at the frontier
@@ -567,7 +569,10 @@ mgw_status mgw_sigma_moments_q(mgw_handle* h, const mgw_options* o, int nocc, in
  * of the MGW_MIXED precision: B' as two BF16 digits, A as seven per-row
  * digits, the 13 digit products above 2^-64 of the top, each exact; the K
  * loop runs in chunks of 128 so that each digit tile loaded serves every
- * product it takes part in.  Error against the exact A B'^T: a few units of
+ * product it takes part in, every level accumulating in its own TMEM
+ * accumulator (exact levels over windows of 4-8 chunks, then added into
+ * 64-bit integers; the two lowest levels in FP32).  K above 65536 runs in
+ * splits summed in FP64.  Error against the exact A B'^T: a few units of
  * 2^-53 times sum_k |A_ik||B'_jk|.  Not in the paper.
  *   A [M][K], B [N][K] in (FP64, row-major);  C [M][N] out (FP64)
  */

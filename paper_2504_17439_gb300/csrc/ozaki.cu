@@ -411,18 +411,20 @@ mgw_status reduce_splits(mgw_handle* h, long count, int nsplit, const double* pa
   return check_launch(h, "reduce_splits");
 }
 
-struct EpiStoreRows {
+struct EpiStoreRows {  // split z of a K-split launch writes C + z split_stride
   double* C;
   long ldc;
-  __device__ bool skip_tile(int, int, int, int) const { return false; }
-  __device__ void operator()(int row_local, int col_base, int m0, int n0, int M, int N,
-                             const long long (&v)[kCols], double*) const {
+  long split_stride;
+  __device__ bool skip_tile(int, int, int, int, int) const { return false; }
+  template <int KC>
+  __device__ void operator()(int row_local, int col_base, int m0, int n0, int M, int N, const long long (&v)[KC],
+                             double*) const {
     const int row = m0 + row_local;
     if (row >= M) return;
 #pragma unroll
-    for (int j = 0; j < kCols; ++j) {
+    for (int j = 0; j < KC; ++j) {
       const int col = n0 + col_base + j;
-      if (col < N) C[(long)row * ldc + col] = __longlong_as_double(v[j]);
+      if (col < N) C[(long)blockIdx.y * split_stride + (long)row * ldc + col] = __longlong_as_double(v[j]);
     }
   }
   __device__ void abort() const {}
@@ -502,7 +504,7 @@ extern "C" mgw_status mgw_gemm_fp64_emu(mgw_handle* h, int M, int N, int K, cons
   CUtensorMap ma, mb;
   MGW_TRY(digit_map(h, &ma, sa, BM));
   MGW_TRY(digit_map(h, &mb, sb, BN));
-  MGW_TRY((ozaki_launch(h, ma, mb, sa.exps, sb.exps, M, N, K, ARowsPlain{}, EpiStoreRows{C, N}, dstatus,
+  MGW_TRY((ozaki_launch(h, ma, mb, sa.exps, sb.exps, M, N, K, ARowsPlain{}, EpiStoreRows{C, N, 0}, dstatus,
                         "gemm_fp64_emu")));
   return tc::check_tc_status(h, dstatus, "mgw_gemm_fp64_emu");
 }
@@ -528,7 +530,7 @@ mgw_status gemm_fp64_tc_nn(mgw_handle* h, int M, int N, int K, const double* A, 
   CUtensorMap ma, mb;
   MGW_TRY(digit_map(h, &ma, sa, BM));
   MGW_TRY(digit_map(h, &mb, sb, BN));
-  MGW_TRY((ozaki_launch(h, ma, mb, sa.exps, sb.exps, M, N, K, ARowsPlain{}, EpiStoreRows{C, ldc}, dstatus, what)));
+  MGW_TRY((ozaki_launch(h, ma, mb, sa.exps, sb.exps, M, N, K, ARowsPlain{}, EpiStoreRows{C, ldc, 0}, dstatus, what)));
   return tc::check_tc_status(h, dstatus, what);
 }
 }  // namespace oz
@@ -539,11 +541,15 @@ extern "C" mgw_status mgw_gemm_mixed(mgw_handle* h, int M, int N, int K, const d
   if (!h) return MGW_ERR_ARG;
   if (M < 1 || N < 1 || K < 1 || !A || !B || !C) return fail(h, MGW_ERR_ARG, "mgw_gemm_mixed: bad arguments");
   MGW_CUDA(h, cudaSetDevice(h->device));
+  // K beyond kMixedMaxK runs in splits, summed from partial products
+  const int nsplit = mixed_min_split(K);
+  const int nz = split_count(K, nsplit);
   Arena ar;
-  double *da, *db, *st;
+  double *da, *db, *st, *part = nullptr;
   ar.add(&da, sliced_doubles(M, K));
   ar.add(&db, sliced_doubles(N, K, kGridSlices));
   ar.add(&st, 3);
+  if (nz > 1) ar.add(&part, (size_t)nz * M * N);
   MGW_TRY(ar.commit(h));
   Sliced sa, sb;
   place_sliced(da, M, K, sa);
@@ -556,9 +562,15 @@ extern "C" mgw_status mgw_gemm_mixed(mgw_handle* h, int M, int N, int K, const d
   MGW_TRY(slice_rows_grid(h, N, K, B, K, gexp, sb));
   CUtensorMap ma, mb;
   MGW_TRY(digit_map(h, &ma, sa, BM));
-  MGW_TRY(digit_map(h, &mb, sb, BN));
-  MGW_TRY((ozaki_mixed_launch<true>(h, ma, mb, sa.exps, sb.exps, M, N, K, ARowsPlain{}, EpiStoreRows{C, N}, dstatus,
-                                    "gemm_mixed")));
+  MGW_TRY(digit_map(h, &mb, sb, kMBN));
+  if (nz == 1) {
+    MGW_TRY((ozaki_mixed_launch<true>(h, ma, mb, sa.exps, sb.exps, M, N, K, ARowsPlain{}, EpiStoreRows{C, N, 0},
+                                      dstatus, "gemm_mixed")));
+  } else {
+    MGW_TRY((ozaki_mixed_launch<true>(h, ma, mb, sa.exps, sb.exps, M, N, K, ARowsPlain{},
+                                      EpiStoreRows{part, N, (long)M * N}, dstatus, "gemm_mixed", nsplit)));
+    MGW_TRY(reduce_splits(h, (long)M * N, nz, part, C, 0));
+  }
   return tc::check_tc_status(h, dstatus, "mgw_gemm_mixed");
 }
 

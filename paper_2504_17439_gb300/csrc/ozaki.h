@@ -126,16 +126,20 @@ __device__ __forceinline__ long long f32_fixed56(float v) {
   return (b >> 31) ? -r : r;
 }
 
-__device__ __forceinline__ double combine_parts(long long acc, long long a67, float v, int E) {
-  const long long hi = acc + (a67 >> 16);
-  const long long lo = ((a67 & 0xFFFF) << 16) + f32_fixed56(v);
+// (hi + lo 2^-32) 2^Ehi as a double for |hi| < 2^63, |lo| < 2^62: lo is
+// folded in at the finest scale 2^(Ehi - sh), sh <= 32, that keeps hi 2^sh
+// below 2^62 (see combine_parts)
+__device__ __forceinline__ double hi_lo_to_double(long long hi, long long lo, int Ehi) {
   const unsigned long long ah = hi < 0 ? 0ull - (unsigned long long)hi : (unsigned long long)hi;
   int sh = ah ? __clzll((long long)ah) - 2 : 32;
   sh = sh > 32 ? 32 : (sh < 0 ? 0 : sh);
   const long long W = (long long)((unsigned long long)hi << sh) +
                       ((lo + (sh < 32 ? (1ll << (31 - sh)) : 0)) >> (32 - sh));
   if (W == 0) return 0.0;
-  return i64_ldexp(W, E - 24 - sh);
+  return i64_ldexp(W, Ehi - sh);
+}
+__device__ __forceinline__ double combine_parts(long long acc, long long a67, float v, int E) {
+  return hi_lo_to_double(acc + (a67 >> 16), ((a67 & 0xFFFF) << 16) + f32_fixed56(v), E - 24);
 }
 
 // The operands may carry different digit counts: SA digits for A, SB for B
@@ -258,7 +262,7 @@ ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant_
   const int m0 = mt * BM, n0 = nt * BN;
   // tiles the epilogue does not need (the lower triangle of a symmetric
   // result) end here, before any barrier, TMEM or shared-memory set-up
-  if (epi.skip_tile(m0, n0, M, N)) return;
+  if (epi.skip_tile(m0, n0, M, N, BN)) return;
   // a wait of an earlier CTA (or launch on this status word) gave up: the
   // result is void, so do no set-up and no work (a failing launch then ends
   // within one wave instead of every CTA waiting out its own limits)
@@ -633,13 +637,14 @@ namespace oz {
 template <class F>
 struct EpiElem {
   F f;
-  __device__ bool skip_tile(int m0, int n0, int M, int N) const { return f.skip_tile(m0, n0, M, N); }
-  __device__ void operator()(int row_local, int col_base, int m0, int n0, int M, int N,
-                             const long long (&v)[kCols], double*) const {
+  __device__ bool skip_tile(int m0, int n0, int M, int N, int bn) const { return f.skip_tile(m0, n0, M, N, bn); }
+  template <int KC>
+  __device__ void operator()(int row_local, int col_base, int m0, int n0, int M, int N, const long long (&v)[KC],
+                             double*) const {
     const int row = m0 + row_local;
     if (row >= M) return;
 #pragma unroll
-    for (int j = 0; j < kCols; ++j) {
+    for (int j = 0; j < KC; ++j) {
       const int col = n0 + col_base + j;
       if (col < N) f(row, col, __longlong_as_double(v[j]));
     }
@@ -649,7 +654,7 @@ struct EpiElem {
 
 struct FStore {  // C[row][col] = alpha v + beta C
   double* C; long ldc; double alpha, beta;
-  __device__ bool skip_tile(int, int, int, int) const { return false; }
+  __device__ bool skip_tile(int, int, int, int, int) const { return false; }
   __device__ void operator()(int r, int c, double v) const {
     double* q = C + (long)r * ldc + c;
     *q = beta == 0.0 ? alpha * v : alpha * v + beta * *q;
@@ -659,12 +664,12 @@ struct FStore {  // C[row][col] = alpha v + beta C
 // (row, col) and (col, row), the rest are dropped, and tiles wholly below the
 // diagonal are skipped (the upper element of each pair lies in a kept tile).
 // Split z of a K-split launch writes the z-th buffer, split_stride apart.
-__host__ __device__ inline bool sym_tile_lower(int m0, int n0, int N) {
-  return (n0 + BN < N ? n0 + BN : N) - 1 < m0;
+__host__ __device__ inline bool sym_tile_lower(int m0, int n0, int N, int bn = BN) {
+  return (n0 + bn < N ? n0 + bn : N) - 1 < m0;
 }
 struct FStoreSym {
   double* C; long ldc; long split_stride;
-  __device__ bool skip_tile(int m0, int n0, int, int N) const { return sym_tile_lower(m0, n0, N); }
+  __device__ bool skip_tile(int m0, int n0, int, int N, int bn) const { return sym_tile_lower(m0, n0, N, bn); }
   __device__ void operator()(int r, int c, double v) const {
     if (r > c) return;
     double* base = C + (long)blockIdx.y * split_stride;
@@ -674,7 +679,7 @@ struct FStoreSym {
 };
 struct FDiagUpdate {  // T[row][col] = T d[col] + alpha v
   double* T; long ldt; const double* d; double alpha;
-  __device__ bool skip_tile(int, int, int, int) const { return false; }
+  __device__ bool skip_tile(int, int, int, int, int) const { return false; }
   __device__ void operator()(int r, int c, double v) const {
     double* q = T + (long)r * ldt + c;
     *q = *q * d[c] + alpha * v;
@@ -685,13 +690,15 @@ struct FDiagUpdate {  // T[row][col] = T d[col] + alpha v
 // tile whose every column has q below its first row is skipped outright (the
 // upper element of each pair lies in a kept tile).  Split z of a K-split
 // launch writes the z-th buffer, split_stride doubles apart.
-__host__ __device__ inline bool sigma_tile_lower(int m0, int n0, int N, int nmo) {
-  const int c1 = (n0 + BN < N ? n0 + BN : N) - 1;
+__host__ __device__ inline bool sigma_tile_lower(int m0, int n0, int N, int nmo, int bn = BN) {
+  const int c1 = (n0 + bn < N ? n0 + bn : N) - 1;
   return n0 / nmo == c1 / nmo && c1 % nmo < m0;
 }
 struct FSigmaN {
   double* sig; int nmo; double beta; long split_stride;
-  __device__ bool skip_tile(int m0, int n0, int, int N) const { return sigma_tile_lower(m0, n0, N, nmo); }
+  __device__ bool skip_tile(int m0, int n0, int, int N, int bn) const {
+    return sigma_tile_lower(m0, n0, N, nmo, bn);
+  }
   __device__ void operator()(int r, int c, double v) const {
     const int n = c / nmo, q = c % nmo;
     if (r > q) return;

@@ -1,32 +1,43 @@
 // The digit-sliced tensor-core GEMM of the mixed precision, with digit tiles
-// reused across products.
+// reused across products and one TMEM accumulator per level.
 //
 // One operand carries 2 digits on a fixed-point grid (the DF tensor, see
 // MGW_MIXED), the other 7 per-row digits; the products kept are the 13 with
-// s + r <= 8 (streamed digit s, resident digit r).  The kernel of ozaki.h
-// loads one A tile and one B tile per digit product, so every tile feeds one
-// MMA and shared memory is written as fast as it is read.  Here the K loop
-// runs in chunks of kCkb K blocks, and inside a chunk level by level
-// (l = 2..8): the 2-digit ("resident") operand of the chunk is loaded once
-// and serves all 13 products, and each digit s of the 7-digit ("streamed")
-// operand is loaded once and serves levels s + 1 and s + 2.  Per K block the
-// copies shrink from 13 (A + B) tiles to 7 streamed + 2 resident.
+// s + r <= 8 (streamed digit s, resident digit r).  The K loop runs in chunks
+// of kCkb K blocks, and inside a chunk level by level (l = 2..8): the
+// 2-digit ("resident") operand of the chunk is loaded once and serves all 13
+// products, and each digit s of the 7-digit ("streamed") operand is loaded
+// once and serves levels s + 1 and s + 2.  Per K block the copies are 7
+// streamed + 2 resident tiles instead of 13 (A + B) pairs.
 //
-// Accumulation is as in ozaki.h, re-cut for the chunk order: each exact
-// level (2..7) of one chunk is a phase in one of two alternating FP32 TMEM
-// accumulators, flushed into 64-bit integers (levels 2..5 in the epilogue
-// warps' registers, 6..7 in TMEM); a chunk holds at most 2 products x kCkb
-// x 64 terms of magnitude <= 2^14 per level, so every phase sum is an
-// integer below 2^22 in its level's unit, exact in FP32 and converted with
-// one FFMA against 1.5 x 2^23.  Level 8 accumulates in a third FP32
-// accumulator over all of K (below 2^-56 of the top, as in ozaki.h).
+// Accumulation.  Every exact level has its own FP32 accumulator in TMEM.  A
+// term of level l is an integer of magnitude <= 2^14 times
+// 2^-8(l-2) (two digits of magnitude <= 2^7), so a chunk adds at most
+// 2 products x 128 terms x 2^14 = 2^22 such units to a level (2^21 to level
+// 2, which has one product).  The exact levels 2..6 therefore accumulate over
+// a window of 4 chunks (8 for level 2) with every partial sum an integer
+// multiple of the level's unit of magnitude <= 2^24 units, exact in FP32; at
+// the end of a window the epilogue warps convert the sum to an integer and
+// add it, in units of level 6 (2^-32), to one 64-bit integer per output
+// element while the MMAs run on.  The windows of levels 3..6 are staggered
+// by one chunk each, so a chunk ends 1.125 windows on average (a flush of
+// every level at every chunk would put six rounds of the epilogue's integer
+// adds on the MMA's critical path).
+// Levels 7 and 8 (below 2^-40 of the top; the digits carry their scales, so
+// the two levels add up in one accumulator) accumulate in FP32 over all of
+// K: one rounding of at most 2^-24 of a partial sum below 2^-25 K of the top
+// unit per MMA.  The final value is the 64-bit sum plus that FP32 sum, rounded
+// once.  K per launch split stays <= kMixedMaxK so that the 64-bit sum (level
+// 2 alone reaches 2^14 K 2^32) cannot overflow.
+//
+// Tile width.  Six accumulators of 64 columns (384 of the 512 TMEM columns,
+// each starting on a multiple of 64) make the tile 128 x 64.
 //
 // CTA (384 threads): warp 0 loads the resident digit sets (two chunks in
-// flight), warps 1-2 the streamed ones (a ring of kRing digit sets, warp 1
-// the even ones, warp 2 the odd), warp 3 allocates TMEM (512 columns) and
-// issues the MMAs, warps 4-11 are the epilogue (as in ozaki.h).  TMEM:
-// accumulators [0,96) and [96,192), level 8 [192,288), levels 6..7 integer
-// words [288,480).  All waits are time-bounded.
+// flight), warps 1-2 the streamed ones (a ring of Lay::kRing digit sets, warp
+// 1 the even ones, warp 2 the odd), warp 3 allocates TMEM (512 columns) and
+// issues the MMAs, warps 4-11 are the epilogue (each owns 32 columns of one
+// row).  All waits are time-bounded.
 #pragma once
 
 #include "ozaki.h"
@@ -34,29 +45,64 @@
 namespace mgw {
 namespace oz {
 
-constexpr int kCkb = 2;    // K blocks per chunk
-constexpr int kRing = 4;   // streamed digit sets in flight
-constexpr int kRSets = 2;  // resident digit sets (chunks) in flight
+constexpr int kMBN = 64;              // tile columns
+constexpr int kMCols = kMBN / 2;      // output columns per epilogue thread
+constexpr int kTailA = 5 * kMBN;      // TMEM columns of the two FP32 tail accumulators (levels 7-8)
+constexpr int kTailB = 6 * kMBN;
+constexpr int kCkb = 2;               // K blocks per chunk
+constexpr int kRSets = 2;             // resident digit sets (chunks) in flight
+constexpr int kWinTop = 6;            // levels 2..6 exact, in windows of chunks
+constexpr int kWinLevels = kWinTop - 1;
+constexpr long kMixedMaxK = 1L << 16;  // K per launch split: |sum| < 2^14 K 2^32 (1 + 2^-7) < 2^63
+
+// window of an exact level: 8 chunks for level 2 (one product), 4 for 3..6,
+// the ends of levels 3..6 staggered so that one of them ends at every chunk
+__host__ __device__ __forceinline__ bool window_end(int c, int l, int nch) {
+  if (c == nch - 1) return true;
+  return l == 2 ? (c & 7) == 7 : ((c + l - 3) & 3) == 3;
+}
+
+// TMEM column of level l's accumulator: the exact levels 2..6 one each,
+// level 7 the first tail accumulator, level 8 the second
+__host__ __device__ __forceinline__ int acc_col(int l) {
+  return l <= kWinTop ? (l - 2) * kMBN : (l == kWinTop + 1 ? kTailA : kTailB);
+}
 
 // kRB: B is the resident (2-digit) operand and A streams (7 digits); else A
 // is resident and B streams.
 template <bool kRB>
 struct MixedLayout {
-  static constexpr int kRRows = kRB ? BN : BM, kSRows = kRB ? BM : BN;
+  static constexpr int kRRows = kRB ? kMBN : BM, kSRows = kRB ? BM : kMBN;
   static constexpr int kRTile = kRRows * BK * 2, kSTile = kSRows * BK * 2;
   static constexpr int kRSet = kGridSlices * kCkb * kRTile;  // both digits of one chunk
   static constexpr int kSSet = kCkb * kSTile;               // one digit of one chunk
   static constexpr int kSOff = kRSets * kRSet;
+  static constexpr int kTail = 1024 + kBarBytes + kMBN * 4;  // alignment slack, barriers, column exponents
+  static constexpr int kRingFit = (232448 - kTail - kSOff) / kSSet;
+  static constexpr int kRing = kRingFit > 8 ? 8 : kRingFit;  // streamed digit sets in flight
   static constexpr int kBarOff = kSOff + kRing * kSSet;
-  static constexpr int kSmem = 1024 + kBarOff + kBarBytes + BN * 4;
+  static constexpr int kSmem = kBarOff + kTail;
+  static_assert(kRing >= 3, "the streamed ring needs three sets to overlap loads with two levels of MMAs");
   static_assert(kSmem <= 232448, "dynamic shared memory above the 227 KB opt-in limit");
   static_assert(kRTile % 1024 == 0 && kSTile % 1024 == 0, "tiles on 1024-byte swizzle atoms");
+  static_assert(kBarOff >= BM * (kMBN + 1) * 8, "the epilogue's staging tile fits in the operand buffers");
+  static_assert((2 * kRSets + 2 * kRing + 2 * kWinLevels + 2) * 8 + 4 <= kBarBytes, "barriers fit");
+  static_assert(kMCols == 32 && kMBN % 64 == 0, "32-column TMEM loads, accumulators on 64-column boundaries");
 };
 
-// integer value of an FP32 phase sum v scaled by `up` (an exact integer of
-// magnitude <= 2^22): the magic 1.5 x 2^23 puts it in the low mantissa bits
-__device__ __forceinline__ int exact_int(float v, float up) {
-  return __float_as_int(fmaf(v, up, 12582912.0f)) - 0x4B400000;
+// the 64-bit sum (units 2^-32 of the top) plus the two FP32 tail sums of
+// levels 7 and 8 (multiples of 2^-48, so exact in units of 2^-64), times 2^E
+__device__ __forceinline__ double combine_windowed(long long acc, float ta, float tb, int E) {
+  return hi_lo_to_double(acc, __float2ll_rn(ta * 0x1p64f) + __float2ll_rn(tb * 0x1p64f), E - 32);
+}
+
+// a window sum of level l (v 2^8(l-2) is its integer), added in units of level 6
+template <int L>
+__device__ __forceinline__ void add_window(long long (&acc)[kMCols], const uint32_t (&w)[kMCols]) {
+  constexpr float up = (float)(1ull << (8 * (L - 2)));
+  constexpr long long scale = 1ll << (8 * (kWinTop - L));
+#pragma unroll
+  for (int j = 0; j < kMCols; ++j) acc[j] += (long long)__float2int_rn(__uint_as_float(w[j]) * up) * scale;
 }
 
 template <bool kRB, class ALoad, class Epi>
@@ -71,15 +117,15 @@ ozaki_mixed_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant
   uint64_t* rfull = reinterpret_cast<uint64_t*>(smem + Lay::kBarOff);  // [kRSets]
   uint64_t* rempty = rfull + kRSets;                                    // [kRSets]
   uint64_t* sfull = rempty + kRSets;                                    // [kRing]
-  uint64_t* sempty = sfull + kRing;                                     // [kRing]
-  uint64_t* accf = sempty + kRing;                                      // [3]: buffers 0, 1 and level 8
-  uint64_t* acce = accf + 3;                                            // [2]
-  uint64_t* drain = acce + 2;
+  uint64_t* sempty = sfull + Lay::kRing;                                // [kRing]
+  uint64_t* accf = sempty + Lay::kRing;    // [kWinLevels + 1]: a window sum of level 2..6; levels 7-8 done
+  uint64_t* acce = accf + kWinLevels + 1;  // [kWinLevels]: a window sum has been read
+  uint64_t* drain = acce + kWinLevels;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
-  int* col_exp = reinterpret_cast<int*>(smem + Lay::kBarOff + kBarBytes);  // [BN]
+  int* col_exp = reinterpret_cast<int*>(smem + Lay::kBarOff + kBarBytes);  // [kMBN]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int MT = (M + BM - 1) / BM, NT = (N + BN - 1) / BN;
+  const int MT = (M + BM - 1) / BM, NT = (N + kMBN - 1) / kMBN;
   int mt, nt;
   if (col_band) {
     const int band = (int)(blockIdx.x / (unsigned)(kBandN * MT));
@@ -94,8 +140,8 @@ ozaki_mixed_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant
     mt = band * kBand + rem % bh;
     nt = rem / bh;
   }
-  const int m0 = mt * BM, n0 = nt * BN;
-  if (epi.skip_tile(m0, n0, M, N)) return;
+  const int m0 = mt * BM, n0 = nt * kMBN;
+  if (epi.skip_tile(m0, n0, M, N, kMBN)) return;
   if (*reinterpret_cast<volatile int*>(status) != kOk) return;
   const int k0 = (int)blockIdx.y * ksplit;
   const int kb_total = (min(ksplit, K - k0) + BK - 1) / BK;
@@ -109,12 +155,12 @@ ozaki_mixed_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant
       mbar_init(&rfull[i], 1);
       mbar_init(&rempty[i], 1);
     }
-    for (int i = 0; i < kRing; ++i) {
+    for (int i = 0; i < Lay::kRing; ++i) {
       mbar_init(&sfull[i], 1);
       mbar_init(&sempty[i], 1);
     }
-    for (int b = 0; b < 3; ++b) mbar_init(&accf[b], 1);
-    for (int b = 0; b < 2; ++b) mbar_init(&acce[b], 8);
+    for (int b = 0; b <= kWinLevels; ++b) mbar_init(&accf[b], 1);
+    for (int b = 0; b < kWinLevels; ++b) mbar_init(&acce[b], 8);
     mbar_init(drain, 1);
     fence_barrier_init();
   }
@@ -169,7 +215,7 @@ ozaki_mixed_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant
       const int kb = chunk_kb(c);
       for (int s = 1; s <= kSlices; ++s, ++g) {
         if ((g & 1) != mine) continue;
-        const int ent = g % kRing, use = g / kRing;
+        const int ent = g % Lay::kRing, use = g / Lay::kRing;
         if (!mbar_wait(&sempty[ent], (use & 1) ^ 1, kWaitNs)) {
           if (lane == 0) atomicCAS(status, kOk, kTimeoutEmpty);
           ok = false;
@@ -188,14 +234,21 @@ ozaki_mixed_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant
       }
     }
     // this warp's sets among the last kRing issued have landed
-    for (int q = (g > kRing ? g - kRing : 0); q < g; ++q)
-      if ((q & 1) == mine && !mbar_wait(&sfull[q % kRing], (q / kRing) & 1, kWaitNs) && lane == 0)
+    for (int q = (g > Lay::kRing ? g - Lay::kRing : 0); q < g; ++q)
+      if ((q & 1) == mine && !mbar_wait(&sfull[q % Lay::kRing], (q / Lay::kRing) & 1, kWaitNs) && lane == 0)
         atomicCAS(status, kOk, kTimeoutDrain);
   } else if (warp == kMmaWarp) {
-    // ---------------- MMA issue: chunk by chunk, level by level
-    const uint32_t idesc = idesc_bf16_f32(BM, BN);
+    // ---------------- MMA issue: chunk by chunk, digit by digit of the
+    // streamed operand.  Digit s takes part in (s, 1) of level s + 1 and
+    // (s, 2) of level s + 2; per K slice the two MMAs go to different
+    // accumulators, so neither waits for the other's result, and when A is
+    // the streamed operand the second one reads A from the collector the
+    // first one filled.  Digit 7 has (7, 1) only: its K slices alternate
+    // between the two tail accumulators.  After digit s, level s + 1 is
+    // complete for the chunk and digit s is free.
+    const uint32_t idesc = idesc_bf16_f32(BM, kMBN);
     bool aborted = false, issued = false;
-    int p = 0;  // exact phases so far
+    unsigned rel = 0;  // bit l - 2: parity of the next completion of acce[l - 2]
     for (int c = 0; c < nch && !aborted; ++c) {
       const int set = c % kRSets, kb = chunk_kb(c);
       if (!mbar_wait(&rfull[set], (c / kRSets) & 1, kWaitNs)) {
@@ -205,67 +258,72 @@ ozaki_mixed_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant
       }
       tc_fence_after();
       const uint32_t rbase = smem_u32(smem + set * Lay::kRSet);
-      for (int l = 2; l <= kLowTop && !aborted; ++l) {
-        const bool exact = l <= kExactTop;
-        const int b = p & 1;
-        uint32_t d;
-        bool first;
-        if (exact) {
-          if (!mbar_wait(&acce[b], ((p >> 1) & 1) ^ 1, kWaitNs)) {
-            if (lane == 0) atomicCAS(status, kOk, kTimeoutEpi);
-            aborted = true;
-            break;
+      for (int s = 1; s <= kSlices && !aborted; ++s) {
+        // exact levels whose first product of the chunk comes with this
+        // digit: level 2 with (1, 1), level s + 2 with (s, 2).  At a window
+        // start their accumulator restarts from zero, once the epilogue has
+        // read the window before.
+        bool zero1 = false, zero2 = false;
+        for (int q = 0; q < 2 && !aborted; ++q) {
+          const int l = q == 0 ? (s == 1 ? 2 : 0) : s + 2;
+          if (l < 2 || l > kWinTop) continue;
+          const bool start = c == 0 || window_end(c - 1, l, nch);
+          (q == 0 ? zero1 : zero2) = start;
+          if (start && c > 0) {
+            if (!mbar_wait(&acce[l - 2], (rel >> (l - 2)) & 1u, kWaitNs)) {
+              if (lane == 0) atomicCAS(status, kOk, kTimeoutEpi);
+              aborted = true;
+              break;
+            }
+            rel ^= 1u << (l - 2);
+            tc_fence_after();
           }
-          tc_fence_after();
-          d = tmem + (uint32_t)(b * BN);
-          first = true;
-        } else {
-          d = tmem + (uint32_t)(2 * BN);
-          first = c == 0;
         }
-        // digit s = l - 1 of this chunk arrives here (the first level using it)
-        if (l - 1 <= kSlices) {
-          const int g = c * kSlices + (l - 2);
-          if (!mbar_wait(&sfull[g % kRing], (g / kRing) & 1, kWaitNs)) {
-            if (lane == 0) atomicCAS(status, kOk, kTimeoutFull);
-            aborted = true;
-            break;
-          }
-          tc_fence_after();
+        if (aborted) break;
+        if (s + 2 > kWinTop && s + 2 <= kLowTop) zero2 = c == 0;  // a tail accumulator's first product
+        const int g = c * kSlices + (s - 1);
+        if (!mbar_wait(&sfull[g % Lay::kRing], (g / Lay::kRing) & 1, kWaitNs)) {
+          if (lane == 0) atomicCAS(status, kOk, kTimeoutFull);
+          aborted = true;
+          break;
         }
-        // products (s, r) = (l - 1, 1) and (l - 2, 2)
-        for (int r = 1; r <= kGridSlices; ++r) {
-          const int s = l - r;
-          if (s < 1 || s > kSlices) continue;
-          const int g = c * kSlices + (s - 1);
-          const uint32_t sbase = smem_u32(smem + Lay::kSOff + (g % kRing) * Lay::kSSet);
-          if (elect_one()) {
-            for (int j = 0; j < kb; ++j) {
-              const uint64_t ds = sdesc_k128(sbase + j * Lay::kSTile);
-              const uint64_t dr = sdesc_k128(rbase + ((r - 1) * kCkb + j) * Lay::kRTile);
+        tc_fence_after();
+        const uint32_t sbase = smem_u32(smem + Lay::kSOff + (g % Lay::kRing) * Lay::kSSet);
+        const uint32_t d1 = tmem + (uint32_t)(acc_col(s + 1)), d2 = tmem + (uint32_t)(acc_col(s + 2));
+        if (elect_one()) {
+          for (int j = 0; j < kb; ++j) {
+            const uint64_t ds = sdesc_k128(sbase + j * Lay::kSTile);
+            const uint64_t dr1 = sdesc_k128(rbase + j * Lay::kRTile);
+            const uint64_t dr2 = sdesc_k128(rbase + (kCkb + j) * Lay::kRTile);
 #pragma unroll
-              for (int kk = 0; kk < BK / 16; ++kk) {
-                const uint64_t da = (kRB ? ds : dr) + (uint64_t)(kk * 2), db = (kRB ? dr : ds) + (uint64_t)(kk * 2);
-                mma_bf16(d, da, db, idesc, (first && j == 0 && kk == 0) ? 0u : 1u);
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              const uint64_t o = (uint64_t)(kk * 2);
+              const bool jk0 = j == 0 && kk == 0;
+              if (s < kSlices) {
+                const uint32_t a1 = zero1 && jk0 ? 0u : 1u, a2 = zero2 && jk0 ? 0u : 1u;
+                if (kRB) {
+                  mma_bf16_fill(d1, ds + o, dr1 + o, idesc, a1);
+                  mma_bf16_lastuse(d2, ds + o, dr2 + o, idesc, a2);
+                } else {
+                  mma_bf16(d1, dr1 + o, ds + o, idesc, a1);
+                  mma_bf16(d2, dr2 + o, ds + o, idesc, a2);
+                }
+              } else {
+                const uint32_t dt = tmem + (uint32_t)(kk & 1 ? kTailB : kTailA);
+                if (kRB) mma_bf16(dt, ds + o, dr1 + o, idesc, 1u);
+                else mma_bf16(dt, dr1 + o, ds + o, idesc, 1u);
               }
             }
           }
-          __syncwarp();
-          first = false;
-          issued = true;
-        }
-        if (elect_one()) {
-          if (exact) mma_commit(&accf[b]);
-          // digit l - 2 served its last product (with r = 2); at level 8 also digit 7
-          if (l >= 3) mma_commit(&sempty[(c * kSlices + (l - 3)) % kRing]);
-          if (l == kLowTop) {
-            mma_commit(&sempty[(c * kSlices + (kSlices - 1)) % kRing]);
+          if (s + 1 <= kWinTop && window_end(c, s + 1, nch)) mma_commit(&accf[s - 1]);
+          mma_commit(&sempty[g % Lay::kRing]);
+          if (s == kSlices) {
             mma_commit(&rempty[set]);
-            if (c == nch - 1) mma_commit(&accf[2]);
+            if (c == nch - 1) mma_commit(&accf[kWinLevels]);
           }
         }
         __syncwarp();
-        if (exact) ++p;
+        issued = true;
       }
     }
     if (aborted && issued) {
@@ -275,104 +333,72 @@ ozaki_mixed_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant
       tc_fence_after();
     }
   } else if (warp >= kEpiWarp0) {
-    // ---------------- epilogue warps 4..11
+    // ---------------- epilogue warps 4..11: tile row quad * 32 + lane,
+    // columns half * 32 .. half * 32 + 31
     const int quad = warp & 3, half = (warp - kEpiWarp0) >> 2;
     const int row_local = quad * 32 + lane;
-    const int col_base = half * kCols;
-    long long acc[kCols];
+    const int col_base = half * kMCols;
+    long long acc[kMCols];
 #pragma unroll
-    for (int j = 0; j < kCols; ++j) acc[j] = 0;
+    for (int j = 0; j < kMCols; ++j) acc[j] = 0;
     const int row = m0 + row_local;
     const int ei = row < M ? ea[row] : 0;
     {
       const int te = threadIdx.x - 32 * kEpiWarp0;
-      if (te < BN) col_exp[te] = n0 + te < N ? eb[n0 + te] : 0;
+      if (te < kMBN) col_exp[te] = n0 + te < N ? eb[n0 + te] : 0;
       named_bar(1, 256);
     }
-    // this thread's 48 elements of the level-6..7 integer accumulator: 96 words
-    const uint32_t lanes = (uint32_t)(quad * 32) << 16;
-    const uint32_t tw = tmem + lanes + (uint32_t)(3 * BN) + (uint32_t)(2 * col_base);
-    {
-      uint32_t z[16];
-#pragma unroll
-      for (int j = 0; j < 16; ++j) z[j] = 0u;
-#pragma unroll
-      for (int c = 0; c < kCols / 8; ++c) tmem_st16u(tw + 16 * c, z);
-    }
+    const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)col_base;
     bool ok = true;
-    int p = 0;
+    unsigned full = 0;  // bit l - 2: parity of the next completion of accf[l - 2]
     for (int c = 0; c < nch && ok; ++c) {
-      for (int l = 2; l <= kExactTop; ++l, ++p) {
-        const int b = p & 1;
-        if (!mbar_wait(&accf[b], (p >> 1) & 1, kWaitNs * 4)) {
+      for (int l = 2; l <= kWinTop; ++l) {
+        if (!window_end(c, l, nch)) continue;
+        if (!mbar_wait(&accf[l - 2], (full >> (l - 2)) & 1u, kWaitNs * 4)) {
           if (lane == 0) atomicCAS(status, kOk, kTimeoutAccum);
           ok = false;
           break;
         }
+        full ^= 1u << (l - 2);
         tc_fence_after();
-        const uint32_t ta = tmem + lanes + (uint32_t)(b * BN + col_base);
-        const float up = __int_as_float((127 + 8 * (l - 2)) << 23);  // 2^8(l-2): v up is the phase's integer
-        if (l <= kRegTop) {
-          const int shift = 8 * (kRegTop - l);
-#pragma unroll
-          for (int q = 0; q < kCols / 16; ++q) {
-            float v[16];
-            tmem_ld16(ta + q * 16, v);
-#pragma unroll
-            for (int j = 0; j < 16; ++j) acc[q * 16 + j] += (long long)exact_int(v[j], up) << shift;
-          }
-        } else {
-          // levels 6..7 in units of 2^-40: the integer scaled by 2^8(7-l)
-          const int shift = 8 * (kExactTop - l);
-#pragma unroll 1
-          for (int q = 0; q < kCols / 16; ++q) {
-            float v[16];
-            tmem_ld16(ta + q * 16, v);
-#pragma unroll
-            for (int hh = 0; hh < 2; ++hh) {
-              uint32_t w[16];
-              tmem_ld16u(tw + 32 * q + 16 * hh, w);
-#pragma unroll
-              for (int j = 0; j < 8; ++j) {
-                long long t = (long long)(((unsigned long long)w[2 * j + 1] << 32) | w[2 * j]);
-                t += (long long)exact_int(v[hh * 8 + j], up) << shift;
-                w[2 * j] = (uint32_t)(unsigned long long)t;
-                w[2 * j + 1] = (uint32_t)((unsigned long long)t >> 32);
-              }
-              tmem_st16u(tw + 32 * q + 16 * hh, w);
-            }
-          }
-        }
+        uint32_t w[kMCols];
+        tmem_ld32(ta + (uint32_t)((l - 2) * kMBN), w);
+        // the accumulator is free for the next window as soon as it is read
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&acce[b]);
+        if (lane == 0) mbar_arrive(&acce[l - 2]);
+        switch (l) {
+          case 2: add_window<2>(acc, w); break;
+          case 3: add_window<3>(acc, w); break;
+          case 4: add_window<4>(acc, w); break;
+          case 5: add_window<5>(acc, w); break;
+          default: add_window<6>(acc, w); break;
+        }
       }
     }
-    if (ok && !mbar_wait(&accf[2], 0, kWaitNs * 4)) {
+    if (ok && !mbar_wait(&accf[kWinLevels], 0, kWaitNs * 4)) {
       if (lane == 0) atomicCAS(status, kOk, kTimeoutAccum);
       ok = false;
     }
     if (ok) {
       tc_fence_after();
-      // value = 2^(e_i + f_j - 16) (acc 2^-24 + acc67 2^-40 + level 8), the
-      // loop rolled with acc[] rotated as in ozaki.h
-      const uint32_t ta = tmem + lanes + (uint32_t)(2 * BN + col_base);
+      // value = 2^(e_i + f_j - 16) (acc 2^-32 + levels 7-8), the loop rolled
+      // with acc[] rotated as in ozaki.h
+      const uint32_t t7 = ta + (uint32_t)kTailA, t8 = ta + (uint32_t)kTailB;
 #pragma unroll 1
-      for (int q = 0; q < kCols / 8; ++q) {
-        float v[8];
-        tmem_ld8(ta + q * 8, v);
-        uint32_t w[16];
-        tmem_ld16u(tw + 16 * q, w);
+      for (int q = 0; q < kMCols / 8; ++q) {
+        float fa[8], fb[8];
+        tmem_ld8(t7 + q * 8, fa);
+        tmem_ld8(t8 + q * 8, fb);
         long long r[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const long long a67 = (long long)(((unsigned long long)w[2 * j + 1] << 32) | w[2 * j]);
-          r[j] = __double_as_longlong(combine_parts(acc[j], a67, v[j], ei + col_exp[col_base + q * 8 + j] - 16));
-        }
+        for (int j = 0; j < 8; ++j)
+          r[j] = __double_as_longlong(
+              combine_windowed(acc[j], fa[j], fb[j], ei + col_exp[col_base + q * 8 + j] - 16));
 #pragma unroll
-        for (int j = 0; j < kCols - 8; ++j) acc[j] = acc[j + 8];
+        for (int j = 0; j < kMCols - 8; ++j) acc[j] = acc[j + 8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[kCols - 8 + j] = r[j];
+        for (int j = 0; j < 8; ++j) acc[kMCols - 8 + j] = r[j];
       }
       tc_fence_before();
       epi(row_local, col_base, m0, n0, M, N, acc, reinterpret_cast<double*>(smem));
@@ -388,23 +414,28 @@ ozaki_mixed_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant
   }
 }
 
-// kRB: B is the 2-digit operand (its map holds 2 digit planes), A the 7-digit
-// one; otherwise the reverse.  Same launch order, K splits and checks as
-// ozaki_launch.
+// splits a launch needs so that K per split stays within kMixedMaxK
+inline int mixed_min_split(long K) { return (int)((K + kMixedMaxK - 1) / kMixedMaxK); }
+
+// kRB: B is the 2-digit operand (its map holds 2 digit planes, box kMBN
+// rows), A the 7-digit one (box BM rows); otherwise A holds 2 digits (box BM
+// rows) and B 7 (box kMBN rows).  Same launch order, K splits and checks as
+// ozaki_launch; K per split must not exceed kMixedMaxK.
 template <bool kRB, class ALoad, class Epi>
 mgw_status ozaki_mixed_launch(mgw_handle* h, const CUtensorMap& mA, const CUtensorMap& mB, const int* ea,
                               const int* eb, int M, int N, int K, const ALoad& al, const Epi& epi, int* dstatus,
                               const char* what, int nsplit = 1) {
-  if (K >= (1 << 24))
-    return fail(h, MGW_ERR_UNSUPPORTED, "%s: K = %d too large for the digit-sliced GEMM", what, K);
   using Lay = MixedLayout<kRB>;
+  const long ksplit = split_kblocks(K, nsplit) * BK;
+  if (ksplit > kMixedMaxK)
+    return fail(h, MGW_ERR_UNSUPPORTED, "%s: K = %d in %d split(s) leaves %ld per split, above %ld", what, K,
+                nsplit, ksplit, kMixedMaxK);
   auto kern = ozaki_mixed_kernel<kRB, ALoad, Epi>;
   static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::kSmem);
   MGW_CUDA(h, attr);
-  const long MT = (M + BM - 1) / BM, NT = (N + BN - 1) / BN;
-  const int ksplit = (int)(split_kblocks(K, nsplit) * BK);
+  const long MT = (M + BM - 1) / BM, NT = (N + kMBN - 1) / kMBN;
   dim3 grid((unsigned)(MT * NT), (unsigned)split_count(K, nsplit), 1);
-  const double rows_a = (double)MT * BM, rows_b = (double)NT * BN;
+  const double rows_a = (double)MT * BM, rows_b = (double)NT * kMBN;
   const double by_rows = rows_a + (double)((MT + kBand - 1) / kBand) * rows_b;
   const double by_cols = (double)((NT + kBandN - 1) / kBandN) * rows_a + rows_b;
   const int col_band = by_cols < by_rows ? 1 : 0;
@@ -414,7 +445,8 @@ mgw_status ozaki_mixed_launch(mgw_handle* h, const CUtensorMap& mA, const CUtens
     cudaEventCreate(&e1);
     cudaEventRecord(e0, h->stream);
   }
-  kern<<<grid, kThreads, Lay::kSmem, h->stream>>>(mA, mB, ea, eb, M, N, K, col_band, ksplit, al, epi, dstatus);
+  kern<<<grid, kThreads, Lay::kSmem, h->stream>>>(mA, mB, ea, eb, M, N, K, col_band, (int)ksplit, al, epi,
+                                                   dstatus);
   mgw_status st = check_launch(h, what);
   if (h->prof) {
     cudaEventRecord(e1, h->stream);

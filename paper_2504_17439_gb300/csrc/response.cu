@@ -271,13 +271,15 @@ static mgw_status response_impl(mgw_handle* h, const mgw_options* o, int nocc, i
   // only, with K = ov split so that the kept tiles fill whole waves
   int w_req = 1, w_nz = 1;
   double* wpart = nullptr;
+  const int wbn = mixed ? oz::kMBN : oz::BN;  // tile columns of the kernel that runs
   if (use_tc) {  // digit planes: V (rows Q, K = ov), V^T (rows ia, K = naux), T and W(t) per order
     int sms = 152;
     MGW_CUDA(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
     long kept = 0;
     for (int m0 = 0; m0 < naux; m0 += oz::BM)
-      for (int n0 = 0; n0 < naux; n0 += oz::BN) kept += oz::sym_tile_lower(m0, n0, naux) ? 0 : 1;
+      for (int n0 = 0; n0 < naux; n0 += wbn) kept += oz::sym_tile_lower(m0, n0, naux, wbn) ? 0 : 1;
     w_req = oz::best_split(kept, ov, sms);
+    if (mixed) w_req = std::max(w_req, oz::mixed_min_split(ov));  // K per split within the mixed kernel's bound
     w_nz = oz::split_count(ov, w_req);
     ar.add(&vd, oz::sliced_doubles(naux, ov, vns));
     ar.add(&vtd, oz::sliced_doubles(ov, naux, vns));
@@ -329,8 +331,8 @@ static mgw_status response_impl(mgw_handle* h, const mgw_options* o, int nocc, i
       MGW_CUDA(h, cudaMemcpyAsync(T0, Lov, sizeof(double) * tsz, cudaMemcpyDeviceToDevice, h->stream));
     }
     CUtensorMap mv, mvt, mt, mw;
-    MGW_TRY(oz::digit_map(h, &mv, sv, oz::BN));
-    MGW_TRY(oz::digit_map(h, &mvt, svt, oz::BN));
+    MGW_TRY(oz::digit_map(h, &mv, sv, wbn));
+    MGW_TRY(oz::digit_map(h, &mvt, svt, wbn));
     MGW_TRY(oz::digit_map(h, &mt, stt, oz::BM));
     MGW_TRY(oz::digit_map(h, &mw, sww, oz::BM));
     // the two products of an order: B = V (rows Q) or V^T (rows ia), 2 digits under MGW_MIXED

@@ -36,7 +36,8 @@ namespace mgw {
 constexpr int kMaxMom = kMaxBinomMom;
 
 // Binomial epilogue of the tensor-core Y stage.  Each of the 256 epilogue
-// threads holds 48 FP64 results of one tile row (t, pl); they are staged in
+// threads holds KC FP64 results of one tile row (t, pl) (the tile has 2 KC
+// columns: 96 on the FP64_TC path, 64 on the mixed one); they are staged in
 // shared memory (the freed pipeline buffers) and recombined per (pl, column).
 // Z(n) = 2 sum_t C(n,t) s^t e^(n-t) Y(t) is a Taylor shift: with e' = s e,
 // repeated a_t += e' a_(t-1) (t descending, nmom - 1 sweeps) turns a_t = Y(t)
@@ -49,23 +50,24 @@ struct EpiBinomialTC {
   int nmom, PB, naux, nmo;
   long ncol;
   double sgn;
-  __device__ bool skip_tile(int, int, int, int) const { return false; }
+  __device__ bool skip_tile(int, int, int, int, int) const { return false; }
+  template <int KC>
   __device__ __forceinline__ void operator()(int row_local, int col_base, int m0, int n0, int, int N,
-                                             const long long (&v)[oz::kCols], double* smem) const {
-    constexpr int LD = oz::BN + 1;
+                                             const long long (&v)[KC], double* smem) const {
+    constexpr int TBN = 2 * KC, LD = TBN + 1;
     const int tid = threadIdx.x - 32 * oz::kEpiWarp0;
-    const int pairs = PB * oz::BN;
+    const int pairs = PB * TBN;
     // eps_x of this thread's next (pl, column) pair, loaded one pair ahead
-    auto eps_of = [&](int pi) { const long n = n0 + pi % oz::BN; return n < N ? eps[n / nmo] : 0.0; };
+    auto eps_of = [&](int pi) { const long n = n0 + pi % TBN; return n < N ? eps[n / nmo] : 0.0; };
     double e_next = tid < pairs ? eps_of(tid) : 0.0;
 #pragma unroll
-    for (int j = 0; j < oz::kCols; ++j) smem[row_local * LD + col_base + j] = __longlong_as_double(v[j]);
+    for (int j = 0; j < KC; ++j) smem[row_local * LD + col_base + j] = __longlong_as_double(v[j]);
     tc::named_bar(1, 256);
     const long g = m0 / 128;
     for (int pi = tid; pi < pairs; pi += 256) {
       const double e_cur = e_next;
       if (pi + 256 < pairs) e_next = eps_of(pi + 256);
-      const int pl = pi / oz::BN, col = pi % oz::BN;
+      const int pl = pi / TBN, col = pi % TBN;
       const long P = g * PB + pl;
       const long n = n0 + col;
       if (P >= naux || n >= N) continue;
@@ -93,12 +95,12 @@ struct EpiBinomialTC {
 
 // K splits of the tensor-core GEMM2 (rows p, columns (n, q), K = nx naux),
 // chosen for its kept (upper-triangle) tiles
-static int gemm2_splits(int nmo, int nmom, long K2, int sms) {
+static int gemm2_splits(int nmo, int nmom, long K2, int sms, int bn) {
   const int MT = (nmo + oz::BM - 1) / oz::BM;
-  const int N = nmom * nmo, NT = (N + oz::BN - 1) / oz::BN;
+  const int N = nmom * nmo, NT = (N + bn - 1) / bn;
   long kept = 0;
   for (int mt = 0; mt < MT; ++mt)
-    for (int nt = 0; nt < NT; ++nt) kept += oz::sigma_tile_lower(mt * oz::BM, nt * oz::BN, N, nmo) ? 0 : 1;
+    for (int nt = 0; nt < NT; ++nt) kept += oz::sigma_tile_lower(mt * oz::BM, nt * bn, N, nmo, bn) ? 0 : 1;
   return oz::best_split(kept, K2, sms);
 }
 
@@ -159,7 +161,13 @@ static mgw_status sigma_impl(mgw_handle* h, const mgw_options* o, int nmo, int n
   // largest chunk, whose K is the largest)
   int sms = 152;
   MGW_CUDA(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
-  const int nsplit_tc = tc ? oz::split_count((long)xc * naux, gemm2_splits(nmo, nmom, (long)xc * naux, sms)) : 1;
+  // (the mixed kernel's tiles are kMBN wide, and its K per split is bounded)
+  const int bn = mixed ? oz::kMBN : oz::BN;
+  auto splits_tc = [&](long K2) {
+    const int r = gemm2_splits(nmo, nmom, K2, sms, bn);
+    return mixed ? std::max(r, oz::mixed_min_split(K2)) : r;
+  };
+  const int nsplit_tc = tc ? oz::split_count((long)xc * naux, splits_tc((long)xc * naux)) : 1;
 
   // tensor-core Y stage: grouped W digits (once) and per-chunk L digits
   const int PBt = std::max(1, 128 / nmom);
@@ -212,7 +220,7 @@ static mgw_status sigma_impl(mgw_handle* h, const mgw_options* o, int nmo, int n
         else
           MGW_TRY(oz::slice_cols(h, ncol, naux, L + (long)x0 * nmo, sx, sl));
         CUtensorMap ml;
-        MGW_TRY(oz::digit_map(h, &ml, sl, oz::BN));
+        MGW_TRY(oz::digit_map(h, &ml, sl, bn));
         auto launch_y = [&](auto epi) {
           if (mixed)
             return oz::ozaki_mixed_launch<true>(h, mw, ml, sw.exps, sl.exps, (int)(ngroups_t * 128), (int)ncol,
@@ -250,10 +258,13 @@ static mgw_status sigma_impl(mgw_handle* h, const mgw_options* o, int nmo, int n
                                  sz2));
         CUtensorMap ma2, mz2;
         MGW_TRY(oz::digit_map(h, &ma2, sa2, oz::BM));
-        MGW_TRY(oz::digit_map(h, &mz2, sz2, oz::BN));
+        MGW_TRY(oz::digit_map(h, &mz2, sz2, bn));
         // upper-triangle tiles only, split along K into partial sums (one
         // buffer per split, summed into Sigma by k_reduce_splits)
-        const int ns2 = std::min(nsplit_tc, gemm2_splits(nmo, nmom, K2, sms));
+        // at most nsplit_tc splits: the K-bounded split count of this chunk
+        // is at most that of the largest chunk, which nsplit_tc covers
+        const int ns2 = std::max(std::min(nsplit_tc, gemm2_splits(nmo, nmom, K2, sms, bn)),
+                                 mixed ? oz::mixed_min_split(K2) : 1);
         const int nz = oz::split_count(K2, ns2);
         auto launch_g2 = [&](const oz::FSigmaN& f, int nsp) {
           const oz::EpiElem<oz::FSigmaN> epi{f};

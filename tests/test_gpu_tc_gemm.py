@@ -48,6 +48,26 @@ def test_fp64_emulated_gemm_matches_fp64(h, M, N, K):
     assert err.max() < 8 * 2.0**-52, err.max()
 
 
+@pytest.mark.parametrize("K", [4800, 1024 * 9])
+def test_mixed_gemm_exact_at_the_window_bound(h, K):
+    """Same-sign operands near the top of their digit ranges make every
+    level's window sum approach the 2^24 units that FP32 holds exactly (K = 9216
+    gives full windows of 8 chunks at level 2): the product must still come out
+    within a few units in the last place of the exact K a b'."""
+    from fractions import Fraction
+    from oracle import mgw_oracle as orc
+
+    M, N = 130, 70
+    a, b = 0.9990234375 - 2.0**-40, 0.99609375 - 2.0**-20
+    A = np.full((M, K), a)
+    B = np.full((N, K), b)
+    C = h.mgw_gemm_mixed(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()).cpu().numpy()
+    bq = float(orc.fixed_point_grid(B)[0, 0])
+    exact = float(Fraction(a) * Fraction(bq) * K)
+    ulp = np.spacing(exact)
+    assert np.abs(C - exact).max() <= 4 * ulp, (np.abs(C - exact).max() / ulp)
+
+
 def test_fp64_emulated_gemm_zero_rows(h):
     A = np.zeros((130, 70))
     B = np.random.default_rng(1).standard_normal((129, 70))
@@ -79,7 +99,7 @@ def test_bounded_wait_gives_up_and_the_handle_stays_usable(h):
 
 
 @pytest.mark.parametrize("M,N,K", [(128, 96, 64), (300, 520, 200), (1, 1, 1), (257, 17, 1000), (512, 384, 4800),
-                                   (130, 140, 2500), (200, 300, 100)])
+                                   (130, 140, 2500), (200, 300, 100), (129, 65, 1088), (130, 70, 65536 + 700)])
 def test_mixed_gemm_is_exact_for_the_rounded_operand(h, M, N, K):
     """The mixed-precision product (chunked, tile-reusing kernel): A at seven
     digits against B rounded to its 16-bit grid (the oracle's
