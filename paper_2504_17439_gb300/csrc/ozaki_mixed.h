@@ -105,6 +105,48 @@ __device__ __forceinline__ void add_window(long long (&acc)[kMCols], const uint3
   for (int j = 0; j < kMCols; ++j) acc[j] += (long long)__float2int_rn(__uint_as_float(w[j]) * up) * scale;
 }
 
+// The MMAs of one streamed digit over the KB K blocks of a chunk, unrolled,
+// every descriptor computed before the first MMA: the tensor pipe takes the
+// next MMA only when the issuing thread reaches it, so the thread runs the
+// MMAs back to back.  pair: the products (s, 1) into d1 and (s, 2) into d2
+// per K slice, the first of each accumulator with a1 / a2 (0: overwrite);
+// otherwise (digit 7) the single product alternating between the two tail
+// accumulators.
+template <bool kRB, class Lay, int KB>
+__device__ __forceinline__ void issue_digit(bool pair, uint32_t d1, uint32_t d2, uint32_t tmem, uint32_t slo,
+                                            uint32_t rlo, uint32_t idesc, uint32_t a1, uint32_t a2) {
+  using namespace tc;
+  constexpr uint32_t kS = Lay::kSTile >> 4, kR = Lay::kRTile >> 4;  // tile strides in descriptor units
+  constexpr int kSteps = KB * (BK / 16);
+  if (pair) {
+#pragma unroll
+    for (int t = 0; t < kSteps; ++t) {
+      const uint32_t j = (uint32_t)(t / (BK / 16)), o = (uint32_t)((t % (BK / 16)) * 2);
+      const uint64_t ds = sdesc_join(slo + j * kS + o);
+      const uint64_t dr1 = sdesc_join(rlo + j * kR + o), dr2 = sdesc_join(rlo + (kCkb + j) * kR + o);
+      const uint32_t f1 = t == 0 ? a1 : 1u, f2 = t == 0 ? a2 : 1u;
+      // (s, 2) first: the run then ends on d1 = level s + 1 and the next
+      // digit starts on level s + 3, never on the accumulator just written
+      if (kRB) {
+        mma_bf16_fill(d2, ds, dr2, idesc, f2);
+        mma_bf16_lastuse(d1, ds, dr1, idesc, f1);
+      } else {
+        mma_bf16(d2, dr2, ds, idesc, f2);
+        mma_bf16(d1, dr1, ds, idesc, f1);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < kSteps; ++t) {
+      const uint32_t j = (uint32_t)(t / (BK / 16)), o = (uint32_t)((t % (BK / 16)) * 2);
+      const uint64_t ds = sdesc_join(slo + j * kS + o), dr1 = sdesc_join(rlo + j * kR + o);
+      const uint32_t dt = tmem + (uint32_t)(t & 1 ? kTailA : kTailB);  // digit 6 ended on tail A
+      if (kRB) mma_bf16(dt, ds, dr1, idesc, 1u);
+      else mma_bf16(dt, dr1, ds, idesc, 1u);
+    }
+  }
+}
+
 template <bool kRB, class ALoad, class Epi>
 __global__ void __launch_bounds__(kThreads, 1)
 ozaki_mixed_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
@@ -245,10 +287,18 @@ ozaki_mixed_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant
     // the streamed operand the second one reads A from the collector the
     // first one filled.  Digit 7 has (7, 1) only: its K slices alternate
     // between the two tail accumulators.  After digit s, level s + 1 is
-    // complete for the chunk and digit s is free.
+    // complete for the chunk and digit s is free.  The tensor pipe takes the
+    // next MMA only when this thread reaches it, so the per-digit work
+    // between MMA runs is kept to a barrier test, bit tests and adds: the
+    // digit loop is unrolled, window starts and ends are bit masks made once
+    // per chunk, and the ring slot advances by one.
     const uint32_t idesc = idesc_bf16_f32(BM, kMBN);
     bool aborted = false, issued = false;
     unsigned rel = 0;  // bit l - 2: parity of the next completion of acce[l - 2]
+    int ent = 0;       // ring slot of the next streamed digit, and its phase parity
+    uint32_t eph = 0;
+    bool ready = false;  // that slot was seen full ahead of time
+    const uint32_t sslot0 = sdesc_lo(smem_u32(smem + Lay::kSOff));  // descriptor low word of ring slot 0
     for (int c = 0; c < nch && !aborted; ++c) {
       const int set = c % kRSets, kb = chunk_kb(c);
       if (!mbar_wait(&rfull[set], (c / kRSets) & 1, kWaitNs)) {
@@ -257,66 +307,57 @@ ozaki_mixed_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant
         break;
       }
       tc_fence_after();
-      const uint32_t rbase = smem_u32(smem + set * Lay::kRSet);
-      for (int s = 1; s <= kSlices && !aborted; ++s) {
+      const uint32_t rlo = sdesc_lo(smem_u32(smem + set * Lay::kRSet));
+      // bit l - 2: a window of level l starts / ends at this chunk
+      unsigned startm = 0, endm = 0;
+#pragma unroll
+      for (int l = 2; l <= kWinTop; ++l) {
+        if (c == 0 || window_end(c - 1, l, nch)) startm |= 1u << (l - 2);
+        if (window_end(c, l, nch)) endm |= 1u << (l - 2);
+      }
+#pragma unroll
+      for (int s = 1; s <= kSlices; ++s) {
         // exact levels whose first product of the chunk comes with this
-        // digit: level 2 with (1, 1), level s + 2 with (s, 2).  At a window
-        // start their accumulator restarts from zero, once the epilogue has
-        // read the window before.
-        bool zero1 = false, zero2 = false;
-        for (int q = 0; q < 2 && !aborted; ++q) {
-          const int l = q == 0 ? (s == 1 ? 2 : 0) : s + 2;
-          if (l < 2 || l > kWinTop) continue;
-          const bool start = c == 0 || window_end(c - 1, l, nch);
-          (q == 0 ? zero1 : zero2) = start;
-          if (start && c > 0) {
+        // digit: level 2 with (1, 1), level s + 2 with (s, 2)
+        const unsigned first = (s == 1 ? 1u : 0u) | (s + 2 <= kWinTop ? 1u << s : 0u);
+        if (c > 0 && (startm & first)) {
+#pragma unroll
+          for (int l = 2; l <= kWinTop; ++l) {
+            if (!((startm & first) >> (l - 2) & 1u)) continue;
             if (!mbar_wait(&acce[l - 2], (rel >> (l - 2)) & 1u, kWaitNs)) {
               if (lane == 0) atomicCAS(status, kOk, kTimeoutEpi);
               aborted = true;
               break;
             }
             rel ^= 1u << (l - 2);
-            tc_fence_after();
           }
+          if (aborted) break;
+          tc_fence_after();
         }
-        if (aborted) break;
-        if (s + 2 > kWinTop && s + 2 <= kLowTop) zero2 = c == 0;  // a tail accumulator's first product
-        const int g = c * kSlices + (s - 1);
-        if (!mbar_wait(&sfull[g % Lay::kRing], (g / Lay::kRing) & 1, kWaitNs)) {
+        const bool zero1 = s == 1 && (startm & 1u);
+        const bool zero2 = s + 2 <= kWinTop ? ((startm >> s) & 1u) != 0 : (s + 2 <= kLowTop && c == 0);
+        if (!ready && !mbar_wait(&sfull[ent], eph, kWaitNs)) {
           if (lane == 0) atomicCAS(status, kOk, kTimeoutFull);
           aborted = true;
           break;
         }
         tc_fence_after();
-        const uint32_t sbase = smem_u32(smem + Lay::kSOff + (g % Lay::kRing) * Lay::kSSet);
-        const uint32_t d1 = tmem + (uint32_t)(acc_col(s + 1)), d2 = tmem + (uint32_t)(acc_col(s + 2));
+        // the next digit's slot, tested now so that the answer is back by the
+        // time this digit's MMAs are issued
+        const int ent_n = ent + 1 == Lay::kRing ? 0 : ent + 1;
+        const uint32_t eph_n = ent + 1 == Lay::kRing ? eph ^ 1u : eph;
+        const bool ready_n = mbar_test(&sfull[ent_n], eph_n);
+        const uint32_t slo = sslot0 + (uint32_t)(ent * (Lay::kSSet >> 4));
+        const int l1 = s + 1, l2 = s + 2;
+        const uint32_t d1 = tmem + (uint32_t)acc_col(l1), d2 = tmem + (uint32_t)acc_col(l2);
         if (elect_one()) {
-          for (int j = 0; j < kb; ++j) {
-            const uint64_t ds = sdesc_k128(sbase + j * Lay::kSTile);
-            const uint64_t dr1 = sdesc_k128(rbase + j * Lay::kRTile);
-            const uint64_t dr2 = sdesc_k128(rbase + (kCkb + j) * Lay::kRTile);
-#pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) {
-              const uint64_t o = (uint64_t)(kk * 2);
-              const bool jk0 = j == 0 && kk == 0;
-              if (s < kSlices) {
-                const uint32_t a1 = zero1 && jk0 ? 0u : 1u, a2 = zero2 && jk0 ? 0u : 1u;
-                if (kRB) {
-                  mma_bf16_fill(d1, ds + o, dr1 + o, idesc, a1);
-                  mma_bf16_lastuse(d2, ds + o, dr2 + o, idesc, a2);
-                } else {
-                  mma_bf16(d1, dr1 + o, ds + o, idesc, a1);
-                  mma_bf16(d2, dr2 + o, ds + o, idesc, a2);
-                }
-              } else {
-                const uint32_t dt = tmem + (uint32_t)(kk & 1 ? kTailB : kTailA);
-                if (kRB) mma_bf16(dt, ds + o, dr1 + o, idesc, 1u);
-                else mma_bf16(dt, dr1 + o, ds + o, idesc, 1u);
-              }
-            }
-          }
-          if (s + 1 <= kWinTop && window_end(c, s + 1, nch)) mma_commit(&accf[s - 1]);
-          mma_commit(&sempty[g % Lay::kRing]);
+          const uint32_t a1 = zero1 ? 0u : 1u, a2 = zero2 ? 0u : 1u;
+          if (kb == kCkb)
+            issue_digit<kRB, Lay, kCkb>(s < kSlices, d1, d2, tmem, slo, rlo, idesc, a1, a2);
+          else
+            issue_digit<kRB, Lay, 1>(s < kSlices, d1, d2, tmem, slo, rlo, idesc, a1, a2);
+          if (l1 <= kWinTop && ((endm >> (l1 - 2)) & 1u)) mma_commit(&accf[l1 - 2]);
+          mma_commit(&sempty[ent]);
           if (s == kSlices) {
             mma_commit(&rempty[set]);
             if (c == nch - 1) mma_commit(&accf[kWinLevels]);
@@ -324,6 +365,9 @@ ozaki_mixed_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant
         }
         __syncwarp();
         issued = true;
+        ent = ent_n;
+        eph = eph_n;
+        ready = __all_sync(0xffffffffu, ready_n);
       }
     }
     if (aborted && issued) {

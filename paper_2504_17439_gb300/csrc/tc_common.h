@@ -54,6 +54,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+// Non-blocking test of the same condition (mbarrier.test_wait never suspends
+// the thread, so it can be issued ahead and its answer used later).
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
 // Wait for the phase with the given parity to complete; false after about
 // `limit_ns`.  The bound is kept in SM cycles (2 per ns, at least limit_ns at
 // any clock up to 2 GHz): clock64 is a register read, whereas %globaltimer is
@@ -118,6 +132,14 @@ __device__ __forceinline__ uint64_t sdesc_k128(uint32_t saddr) {
   d |= (uint64_t)2 << 61;                         // 128-byte swizzle
   return d;
 }
+
+// The same descriptor as two 32-bit words: the high word is one constant,
+// the low word (start address >> 4, leading byte offset) takes offsets by a
+// 32-bit add (the 14-bit address field cannot carry below 256 KB of shared
+// memory), so a run of MMAs needs no 64-bit arithmetic per descriptor.
+constexpr uint32_t kSdescHi = (uint32_t)(1024 >> 4) | (1u << 14) | (2u << 29);
+__device__ __forceinline__ uint32_t sdesc_lo(uint32_t saddr) { return ((saddr & 0x3FFFF) >> 4) | (1u << 16); }
+__device__ __forceinline__ uint64_t sdesc_join(uint32_t lo) { return ((uint64_t)kSdescHi << 32) | lo; }
 
 // Instruction descriptor: kind::f16 with BF16 A and B (K-major), FP32 accumulate.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
