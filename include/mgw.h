@@ -255,6 +255,15 @@ mgw_status mgw_qp_solve(mgw_handle* h, const mgw_options* o,
  * and later calls with the same table (sizes and pointers) and workspace
  * replay it on the handle's stream.  The graph reads the inputs' current
  * contents; it is rebuilt when the table, nmom or the workspace changes.
+ * With o->precision == MGW_MIXED the stages are the same on the tensor cores:
+ * one grouped launch of the mixed digit-sliced kernel per stage over all
+ * systems (tensor maps and epilogue parameters per system in a device table),
+ * the digit slicing between stages per system, the whole sequence captured as
+ * one CUDA graph (o->batch_graph) and replayed; the rounds of Green's-function
+ * indices are the fewest that fit half of the free device memory.  Results
+ * as mgw_response_moments + mgw_sigma_moments under MGW_MIXED per system.
+ * Needs nmom <= 16 and nocc nvir, naux <= 65536.  The call returns after the
+ * work has finished (it reads the wait status).
  * With o->precision == MGW_FP64_TC each system instead runs the
  * single-system FP64-accurate tensor-core pipeline (mgw_response_moments and
  * mgw_sigma_moments), the systems spread, largest first, over four internal

@@ -242,6 +242,7 @@ mgw_status mgw_destroy(mgw_handle* h) {
   cudaStreamSynchronize(h->stream);
   clear_spans(h);
   if (h->batched_plan_free) h->batched_plan_free(h->batched_plan);
+  if (h->mixed_plan_free) h->mixed_plan_free(h->mixed_plan);
   if (h->chain_pool_free) h->chain_pool_free(h->chain_pool);
   if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
   for (auto& sl : h->slots)

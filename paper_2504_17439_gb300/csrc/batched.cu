@@ -356,7 +356,8 @@ extern "C" mgw_status mgw_sigma_moments_batched(mgw_handle* h, const mgw_options
     h->batched_plan = new BatchedPlan();
     h->batched_plan_free = free_plan;
   }
-  if (o->precision == MGW_FP64_TC || o->precision == MGW_MIXED)
+  if (o->precision == MGW_MIXED) return sigma_moments_batched_mixed(h, o, nsys, nmom, sys);
+  if (o->precision == MGW_FP64_TC)
     return batched_tc(h, static_cast<BatchedPlan*>(h->batched_plan), o, nsys, nmom, sys);
   const int rounds = 4;  // Green's-function chunks per sector and system
 

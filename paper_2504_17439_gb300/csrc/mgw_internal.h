@@ -31,6 +31,10 @@ struct mgw_handle {
   // table, replayed while it is unchanged; a stream of its own to capture on
   void* batched_plan = nullptr;
   void (*batched_plan_free)(void*) = nullptr;
+  // mixed-precision batched build (batched_mixed.cu): workspace, item tables
+  // and the captured graph of the last problem table
+  void* mixed_plan = nullptr;
+  void (*mixed_plan_free)(void*) = nullptr;
   // whole-chain batches (batched_chain.cu): sub-handles driven by host threads
   void* chain_pool = nullptr;
   void (*chain_pool_free)(void*) = nullptr;
@@ -409,6 +413,10 @@ mgw_status potrf_potrs(mgw_handle* h, int n, double* a, int nrhs, double* b, boo
 
 // Small elementwise kernels
 mgw_status energy_differences(mgw_handle* h, int nocc, int nvir, const double* eps, double* D);
+// mgw_sigma_moments_batched under MGW_MIXED: one grouped tensor-core launch
+// per stage over all systems (batched_mixed.cu)
+mgw_status sigma_moments_batched_mixed(mgw_handle* h, const mgw_options* o, int nsys, int nmom,
+                                       const mgw_system* sys);
 mgw_status scale_columns(mgw_handle* h, long rows, long cols, const double* src, const double* d,
                          double* dst);  // dst[r][c] = src[r][c] * d[c]
 mgw_status add_identity(mgw_handle* h, int n, double* a, double s);  // a += s * I

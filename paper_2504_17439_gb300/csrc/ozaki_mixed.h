@@ -147,11 +147,13 @@ __device__ __forceinline__ void issue_digit(bool pair, uint32_t d1, uint32_t d2,
   }
 }
 
+// One tile of the product: `tile` is the tile's index in the launch order
+// (row or column bands), k0 / ksplit the K range.  The tensor maps may sit in
+// the kernel's parameters or in global memory (grouped launches).
 template <bool kRB, class ALoad, class Epi>
-__global__ void __launch_bounds__(kThreads, 1)
-ozaki_mixed_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
-                   const int* __restrict__ ea, const int* __restrict__ eb, int M, int N, int K, int col_band,
-                   int ksplit, ALoad al, Epi epi, int* status) {
+__device__ __forceinline__ void mixed_tile(const CUtensorMap* pA, const CUtensorMap* pB, const int* __restrict__ ea,
+                                           const int* __restrict__ eb, int M, int N, int K, long tile, int col_band,
+                                           int k0, int ksplit, const ALoad& al, const Epi& epi, int* status) {
   using namespace tc;
   using Lay = MixedLayout<kRB>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -170,14 +172,14 @@ ozaki_mixed_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant
   const int MT = (M + BM - 1) / BM, NT = (N + kMBN - 1) / kMBN;
   int mt, nt;
   if (col_band) {
-    const int band = (int)(blockIdx.x / (unsigned)(kBandN * MT));
-    const int rem = (int)(blockIdx.x % (unsigned)(kBandN * MT));
+    const int band = (int)(tile / (kBandN * (long)MT));
+    const int rem = (int)(tile % (kBandN * (long)MT));
     const int bw = min(kBandN, NT - band * kBandN);
     nt = band * kBandN + rem % bw;
     mt = rem / bw;
   } else {
-    const int band = (int)(blockIdx.x / (unsigned)(kBand * NT));
-    const int rem = (int)(blockIdx.x % (unsigned)(kBand * NT));
+    const int band = (int)(tile / (kBand * (long)NT));
+    const int rem = (int)(tile % (kBand * (long)NT));
     const int bh = min(kBand, MT - band * kBand);
     mt = band * kBand + rem % bh;
     nt = rem / bh;
@@ -185,12 +187,11 @@ ozaki_mixed_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant
   const int m0 = mt * BM, n0 = nt * kMBN;
   if (epi.skip_tile(m0, n0, M, N, kMBN)) return;
   if (*reinterpret_cast<volatile int*>(status) != kOk) return;
-  const int k0 = (int)blockIdx.y * ksplit;
   const int kb_total = (min(ksplit, K - k0) + BK - 1) / BK;
   const int nch = (kb_total + kCkb - 1) / kCkb;
   const int r0 = kRB ? n0 : m0, s0 = kRB ? m0 : n0;  // first row of the resident / streamed operand
-  const CUtensorMap* mR = kRB ? &mB : &mA;
-  const CUtensorMap* mS = kRB ? &mA : &mB;
+  const CUtensorMap* mR = kRB ? pB : pA;
+  const CUtensorMap* mS = kRB ? pA : pB;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < kRSets; ++i) {
@@ -219,8 +220,8 @@ ozaki_mixed_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant
   if (warp == 0) {
     // ---------------- resident digit sets: both digits of chunk c into set c % kRSets
     if (elect_one()) {
-      prefetch_tmap(&mA);
-      prefetch_tmap(&mB);
+      prefetch_tmap(pA);
+      prefetch_tmap(pB);
     }
     __syncwarp();
     int c = 0;
@@ -456,6 +457,52 @@ ozaki_mixed_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant
     tc_fence_after();
     tmem_dealloc(tmem, 512);
   }
+}
+
+template <bool kRB, class ALoad, class Epi>
+__global__ void __launch_bounds__(kThreads, 1)
+ozaki_mixed_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
+                   const int* __restrict__ ea, const int* __restrict__ eb, int M, int N, int K, int col_band,
+                   int ksplit, ALoad al, Epi epi, int* status) {
+  mixed_tile<kRB>(&mA, &mB, ea, eb, M, N, K, (long)blockIdx.x, col_band, (int)blockIdx.y * ksplit, ksplit, al, epi,
+                  status);
+}
+
+// One problem of a grouped launch: its operands' tensor maps (in global
+// memory, written before the launch), exponents, sizes, launch order and
+// epilogue.  K stays whole (<= kMixedMaxK).
+template <class Epi>
+struct alignas(64) MixedItem {
+  CUtensorMap mA, mB;
+  const int* ea;
+  const int* eb;
+  int M, N, K, col_band;
+  Epi epi;
+};
+
+// Many independent products of one kind in one launch: CTA x finds its
+// problem b by bisection of the tile prefix sums (start[b] <= x <
+// start[b + 1]) and runs that problem's tile x - start[b].
+template <bool kRB, class Epi>
+__global__ void __launch_bounds__(kThreads, 1)
+ozaki_mixed_grouped_kernel(const MixedItem<Epi>* __restrict__ items, const long* __restrict__ start, int nitems,
+                           int* status) {
+  const long x = (long)blockIdx.x;
+  int lo = 0, hi = nitems - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (start[mid] <= x) lo = mid;
+    else hi = mid - 1;
+  }
+  const MixedItem<Epi>* it = items + lo;
+  if (threadIdx.x == 0) {  // the maps were written through the generic proxy
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&it->mA) : "memory");
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&it->mB) : "memory");
+  }
+  __syncthreads();
+  const Epi epi = it->epi;
+  mixed_tile<kRB>(&it->mA, &it->mB, it->ea, it->eb, it->M, it->N, it->K, x - start[lo], it->col_band, 0, it->K,
+                  ARowsPlain{}, epi, status);
 }
 
 // splits a launch needs so that K per split stays within kMixedMaxK

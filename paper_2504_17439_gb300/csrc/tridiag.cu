@@ -20,10 +20,11 @@
 // tridiagonal solve with every eigenvector and the back-transformation of
 // all of them; here only nrows of n rows are ever formed.
 //
-// The 32-bit dense solver API takes matrices of up to 2^31 bytes: ormtr
-// refused n = 36 499 (cusolver status 3, invalid value, for any number of
-// columns).  Beyond that size the 64-bit syevd (Xsyevd) runs instead, with
-// every eigenvector, and its first nrows rows are copied out.
+// The 32-bit dense solver API refuses some large matrices: ormtr answered
+// status 3 (invalid value) at n = 36 499 for any number of columns, while
+// n = 20 400 runs.  Where its workspace queries refuse the size, the 64-bit
+// syevd (Xsyevd) runs instead, with every eigenvector, and its first nrows
+// rows are copied out.
 #include "mgw_internal.h"
 #include "ozaki.h"
 
@@ -282,7 +283,16 @@ static mgw_status eig_dense_64(mgw_handle* h, int n, int nrows, double* H, doubl
 
 mgw_status eig_physical_rows(mgw_handle* h, int n, int nrows, double* H, double* E, double* chi, long ldchi) {
   if (n <= 0) return MGW_OK;
-  if ((long)n * n > (1L << 31) / (long)sizeof(double)) return eig_dense_64(h, n, nrows, H, E, chi, ldchi);
+  // workspace queries first: where the 32-bit routines refuse the size, the
+  // 64-bit syevd runs instead (the queries read no data; H stands in for
+  // every device pointer they take)
+  int lwork = 0, lw2 = 0;
+  const bool fits32 =
+      cusolverDnDsytrd_bufferSize(h->solver, CUBLAS_FILL_MODE_LOWER, n, H, n, H, H, H, &lwork) ==
+          CUSOLVER_STATUS_SUCCESS &&
+      cusolverDnDormtr_bufferSize(h->solver, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, n, nrows, H, n,
+                                  H, H, n, &lw2) == CUSOLVER_STATUS_SUCCESS;
+  if (!fits32) return eig_dense_64(h, n, nrows, H, E, chi, ldchi);
   const long n2 = (long)n * n;
   const int nb = std::min(n, 4096);  // eigenvectors per inverse-iteration batch
   double *d, *e, *e2, *tau, *bounds, *P, *Z, *U0, *U1, *U2, *ML;
@@ -303,10 +313,6 @@ mgw_status eig_physical_rows(mgw_handle* h, int n, int nrows, double* H, double*
   PV = reinterpret_cast<unsigned char*>(pvd);
 
   // 1. H = Q T Q^T (lower storage; H is symmetric, row- and column-major alike)
-  int lwork = 0, lw2 = 0;
-  MGW_SOLVER(h, cusolverDnDsytrd_bufferSize(h->solver, CUBLAS_FILL_MODE_LOWER, n, H, n, d, e, tau, &lwork));
-  MGW_SOLVER(h, cusolverDnDormtr_bufferSize(h->solver, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, n,
-                                            nrows, H, n, tau, P, n, &lw2));
   lwork = std::max(std::max(lwork, lw2), 1);
   double* work;
   MGW_TRY(slot_buffer(h, 82, (size_t)lwork, &work));

@@ -105,6 +105,38 @@ def test_batched_tensor_core_path_matches_oracle():
     h.close()
 
 
+def test_batched_mixed_grouped_launches_match_oracle():
+    """The mixed-precision batch (one grouped tensor-core launch per stage over
+    all systems, replayed from a CUDA graph on the second call) against the
+    oracle on the tensors the mixed path contracts (V and L rounded to their
+    own 16-bit grids), at the FP64 parity tolerance, per system."""
+    from paper_2504_17439_gb300 import build, mgw
+
+    build.build()
+    h = mgw.Handle(0)
+    shapes = mgw_inputs.batch_shapes(7, seed=83, nmo_lo=10, nmo_hi=70, nmom_max=2)
+    nmom = 6
+    systems, refs = [], []
+    for i, sh in enumerate(shapes):
+        eps = mgw_inputs.orbital_energies(sh.nocc, sh.nvir, 850 + i)
+        L = mgw_inputs.df_tensor(sh.naux, sh.nmo, 850 + i) * 2.0
+        V = orc.particle_hole_block(L, sh.nocc)
+        W = orc.tda_response_moments(orc.fixed_point_grid(V), orc.energy_differences(eps, sh.nocc), nmom)
+        refs.append(orc.sigma_moments(eps, sh.nocc, orc.fixed_point_grid(L), W))
+        systems.append(dict(nocc=sh.nocc, nvir=sh.nvir, naux=sh.naux, eps=torch.from_numpy(eps).cuda(),
+                            L=torch.from_numpy(L).cuda()))
+    o = mgw.options(precision=mgw.MGW_MIXED)
+    outs = None
+    for call in range(2):
+        outs = h.mgw_sigma_moments_batched(o, nmom, systems, out=outs)
+        for (gh, gp), (rh, rp) in zip(outs, refs):
+            gh, gp = gh.cpu().numpy(), gp.cpu().numpy()
+            for n in range(nmom):
+                assert rel(gh[n], rh[n]) < 1e-9, (call, n)
+                assert rel(gp[n], rp[n]) < 1e-9, (call, n)
+    h.close()
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp64_tc"])
 def test_g0w0_and_response_batched_match_single_system_calls(precision):
     """The whole-chain batch (sub-handles on host threads) gives each system
