@@ -606,8 +606,10 @@ def run_gpu(args):
 
 def run_batched(args):
     """Uneven batch (nmo ~ U{40..300}, nocc = round(nmo/6), naux = 4 nmo,
-    nmom_max 5, TDA): the grouped build of all systems vs one system at a time
-    through the single-system entry points; systems per second of each."""
+    nmom_max 5, TDA, MGW_MIXED): every stage of every system's response and
+    Sigma build as one grouped tensor-core launch over all systems, replayed
+    from a CUDA graph, against the same systems one at a time through the
+    single-system entry points (mixed, and plain FP64); systems per second."""
     import torch
 
     from paper_2504_17439_gb300 import build, mgw
@@ -622,15 +624,15 @@ def run_batched(args):
         systems.append(dict(nocc=sh.nocc, nvir=sh.nvir, naux=sh.naux, eps=torch.from_numpy(eps).cuda(),
                             L=torch.from_numpy(L).cuda()))
     h = mgw.Handle(0)
-    o = mgw.options()
+    om, o64 = mgw.options(precision=mgw.MGW_MIXED), mgw.options()
     stream = torch.cuda.current_stream()
 
-    outs = h.mgw_sigma_moments_batched(o, nmom, systems)  # tunes tile shapes, captures the graph
+    outs = h.mgw_sigma_moments_batched(om, nmom, systems)  # tables, then the captured graph
 
-    def grouped():
-        return h.mgw_sigma_moments_batched(o, nmom, systems, out=outs)
+    def grouped_mixed():
+        return h.mgw_sigma_moments_batched(om, nmom, systems, out=outs)
 
-    def sequential():
+    def sequential(o):
         out = []
         for sy in systems:
             Lov = h.mgw_extract_ov(sy["nocc"], sy["nvir"], sy["L"])
@@ -638,58 +640,43 @@ def run_batched(args):
             out.append(h.mgw_sigma_moments(o, sy["nocc"], sy["nvir"], sy["naux"], nmom, sy["eps"], sy["L"], W))
         return out
 
-    otc = mgw.options(precision=mgw.MGW_FP64_TC)
-    outs_tc = h.mgw_sigma_moments_batched(otc, nmom, systems)
-
-    def batched_tc():
-        return h.mgw_sigma_moments_batched(otc, nmom, systems, out=outs_tc)
-
-    def sequential_tc():
-        out = []
-        for sy in systems:
-            Lov = h.mgw_extract_ov(sy["nocc"], sy["nvir"], sy["L"])
-            W = h.mgw_response_moments(otc, sy["nocc"], sy["nvir"], sy["naux"], nmom, sy["eps"], Lov)
-            out.append(h.mgw_sigma_moments(otc, sy["nocc"], sy["nvir"], sy["naux"], nmom, sy["eps"], sy["L"], W))
-        return out
-
-    from paper_2504_17439_gb300 import driver
-
-    def g0w0_batched_tc():  # the whole chain: moments, Lanczos, QP solve
-        return h.mgw_g0w0_batched(otc, 5, systems)
-
-    def g0w0_sequential_tc():
-        return [driver.g0w0(h, sy["eps"], sy["L"], sy["nocc"], 5, opts=mgw.options(precision=mgw.MGW_FP64_TC))
-                for sy in systems]
-
-    res = {}
-    for name, fn in (("batched_tc", batched_tc), ("sequential_tc", sequential_tc), ("grouped", grouped),
-                     ("sequential", sequential), ("g0w0_batched_tc", g0w0_batched_tc),
-                     ("g0w0_sequential_tc", g0w0_sequential_tc)):
-        for _ in range(args.warmup):
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
             fn()
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             fn()
         b.record(stream)
         b.synchronize()
-        res[name] = a.elapsed_time(b) / 1e3 / args.steps
-    g, sq, btc = grouped(), sequential(), batched_tc()
-    diff = max(float((x[0] - y[0]).abs().max() / y[0].abs().max()) for x, y in zip(g, sq))
-    diff_tc = max(max(float((x[0] - y[0]).abs().max() / y[0].abs().max()),
-                      float((x[1] - y[1]).abs().max() / y[1].abs().max())) for x, y in zip(btc, sq))
-    line = {"metric": "batched_sigma_build_systems_per_s", "value": len(systems) / res["batched_tc"],
+        return a.elapsed_time(b) / 1e3 / steps
+
+    n0 = h.launches
+    grouped_mixed()
+    torch.cuda.synchronize()
+    launches = h.launches - n0
+    res = {"grouped_mixed": timed(grouped_mixed, args.steps, args.warmup),
+           "sequential_mixed": timed(lambda: sequential(om), 1, 1),
+           "sequential_fp64": timed(lambda: sequential(o64), 1, 0)}
+    g, sm, s64 = grouped_mixed(), sequential(om), sequential(o64)
+    diff_mixed = max(max(float((x[k] - y[k]).abs().max() / y[k].abs().max()) for k in (0, 1))
+                     for x, y in zip(g, sm))
+    diff_fp64 = max(max(float((x[k] - y[k]).abs().max() / y[k].abs().max()) for k in (0, 1))
+                    for x, y in zip(g, s64))
+    line = {"metric": "batched_sigma_build_systems_per_s", "value": len(systems) / res["grouped_mixed"],
             "unit": "systems/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
-            "dtype": "bf16 digit products -> f64", "data": "synthetic",
+            "dtype": "bf16 digit products -> f64 (L as bf16 hi/lo on one grid)", "data": "synthetic",
             "config": {"workload": "batch", "systems": len(systems), "nmo": [s.nmo for s in shapes][:8] + ["..."],
-                       "nmom_max": 5, "path": "tensor-core pipeline per system over 4 concurrent streams"},
+                       "nmom_max": 5, "screening": "tda", "precision": "mixed",
+                       "path": "one grouped tensor-core launch per stage over all systems, CUDA graph replay"},
+            "gpu_launches": launches,
             "systems_per_s": {k: len(systems) / v for k, v in res.items()},
-            "speedup_vs_sequential_fp64": res["sequential"] / res["batched_tc"],
-            "fp64_grouped_graph_vs_sequential_fp64": res["sequential"] / res["grouped"],
-            "g0w0_chain_batched_vs_sequential": res["g0w0_sequential_tc"] / res["g0w0_batched_tc"],
-            "max_rel_diff_fp64_grouped_vs_sequential": diff,
-            "max_rel_diff_tc_batched_vs_fp64_sequential": diff_tc}
+            "seconds": res,
+            "speedup_vs_sequential_fp64": res["sequential_fp64"] / res["grouped_mixed"],
+            "speedup_vs_sequential_mixed": res["sequential_mixed"] / res["grouped_mixed"],
+            "max_rel_diff_vs_sequential_mixed": diff_mixed,
+            "max_rel_diff_vs_sequential_fp64": diff_fp64}
     print(json.dumps(line), flush=True)
     h.close()
     return 0

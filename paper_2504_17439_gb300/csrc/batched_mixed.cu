@@ -11,9 +11,11 @@
 // and replayed while the systems' sizes and pointers stay the same.
 //
 // Launch order per product (row or column bands) is chosen per item as in
-// ozaki_mixed_launch; the rounds of Green's-function indices are the fewest
-// that keep every GEMM2's K within the kernel's bound and the per-round
-// buffers of all systems within half of the free device memory.
+// ozaki_mixed_launch.  The Green's-function indices of every system are split
+// evenly over the fewest rounds whose buffers (all systems' chunks of Z and
+// their digits are live in a round) fit in 60% of the free device memory,
+// each chunk within GEMM2's K bound; a round's launches hold the systems that
+// still have a chunk.
 #include "mgw_internal.h"
 #include "ozaki_mixed.h"
 #include "sigma_epi.h"
@@ -26,8 +28,7 @@
 namespace mgw {
 namespace {
 
-constexpr int kBinomMax = 16;  // nmom <= 16 (N <= 7)
-using EpiY = EpiBinomialTC<kBinomMax>;
+constexpr int kBinomMax = 16;  // nmom <= 16 (N <= 7); the Y epilogue's sweeps are unrolled to 12 or 16
 using EpiW = oz::EpiElem<oz::FStoreSym>;
 using EpiT = oz::EpiElem<oz::FDiagUpdate>;
 using EpiG = oz::EpiElem<oz::FSigmaN>;
@@ -72,6 +73,7 @@ struct MixedPlan {
   std::vector<SysWs> S;
   std::vector<Stage> stages;
   int rounds = 1;
+  long graph_launches = 0;
   int* dstatus = nullptr;
   cudaGraphExec_t exec = nullptr;
   ~MixedPlan() {
@@ -94,6 +96,7 @@ int band_order(long M, long N) {  // as ozaki_mixed_launch: the order that fetch
 // (tab == nullptr): one walk for both, so the two always agree.  The slicing
 // between stages runs only when issuing; the tensor maps are encoded only
 // when building.
+template <class EpiY>
 struct Walker {
   mgw_handle* h;
   MixedPlan* P;
@@ -285,15 +288,20 @@ size_t system_doubles(const mgw_system& s, int nmom, const long xc[2]) {
   return n + 64 * 16;  // alignment of each buffer
 }
 
+// Green's-function indices per round of one system for `rounds` rounds: an
+// even split of each sector, capped by GEMM2's K bound (xc naux <=
+// kMixedMaxK); a system whose cap forces more rounds takes them
 void rounds_xc(const mgw_system& s, int rounds, long xc[2]) {
-  xc[0] = std::max(1L, ((long)s.nocc + rounds - 1) / rounds);
-  xc[1] = std::max(1L, ((long)s.nvir + rounds - 1) / rounds);
+  const long kcap = std::max(1L, oz::kMixedMaxK / std::max(1, s.naux));
+  const long nx[2] = {(long)s.nocc, (long)s.nvir};
+  for (int sec = 0; sec < 2; ++sec) xc[sec] = std::max(1L, std::min(kcap, (nx[sec] + rounds - 1) / rounds));
 }
 
 }  // namespace
 
-mgw_status sigma_moments_batched_mixed(mgw_handle* h, const mgw_options* o, int nsys, int nmom,
-                                       const mgw_system* sys) {
+namespace {
+template <class EpiY>
+mgw_status batched_mixed(mgw_handle* h, const mgw_options* o, int nsys, int nmom, const mgw_system* sys) {
   if (nmom > kBinomMax)
     return fail(h, MGW_ERR_UNSUPPORTED, "mgw_sigma_moments_batched: MGW_MIXED takes nmom <= %d", kBinomMax);
   for (int s = 0; s < nsys; ++s)
@@ -316,23 +324,26 @@ mgw_status sigma_moments_batched_mixed(mgw_handle* h, const mgw_options* o, int 
     if (P->exec) cudaGraphExecDestroy(P->exec);
     P->exec = nullptr;
     P->key.clear();
-    // rounds: the fewest that keep every K2 = xc naux <= kMixedMaxK and the
-    // workspace within half of the free memory
+    // rounds: the fewest whose per-round buffers of all systems fit in 60%
+    // of the free memory (every system split evenly over them, within GEMM2's
+    // K bound)
     size_t free_b = 0, total_b = 0;
     MGW_CUDA(h, cudaMemGetInfo(&free_b, &total_b));
-    const size_t budget = (free_b + P->dmem_bytes) / 2;
-    int rounds = 1;
+    const size_t budget = (size_t)(0.6 * (double)(free_b + P->dmem_bytes));
+    long max_nx = 1;
+    for (int s = 0; s < nsys; ++s) max_nx = std::max(max_nx, (long)std::max(sys[s].nocc, sys[s].nvir));
+    int split = 1, rounds = 1;
     size_t need = 0;
-    for (;; rounds *= 2) {
+    for (split = 1; split <= max_nx; ++split) {
       need = 0;
-      bool kfit = true;
+      rounds = 1;
       for (int s = 0; s < nsys; ++s) {
         long xc[2];
-        rounds_xc(sys[s], rounds, xc);
-        kfit = kfit && std::max(xc[0], xc[1]) * sys[s].naux <= oz::kMixedMaxK;
+        rounds_xc(sys[s], split, xc);
         need += system_doubles(sys[s], nmom, xc) * sizeof(double);
+        rounds = std::max(rounds, (int)std::max((sys[s].nocc + xc[0] - 1) / xc[0], (sys[s].nvir + xc[1] - 1) / xc[1]));
       }
-      if ((kfit && need <= budget) || rounds > 4096) break;
+      if (need <= budget) break;
     }
     if (need > budget)
       return fail(h, MGW_ERR_NOMEM, "mgw_sigma_moments_batched: %zu bytes of workspace above the budget", need);
@@ -359,7 +370,7 @@ mgw_status sigma_moments_batched_mixed(mgw_handle* h, const mgw_options* o, int 
       q.nmo = sys[s].nocc + sys[s].nvir;
       q.ov = (long)sys[s].nocc * sys[s].nvir;
       q.naux = sys[s].naux;
-      rounds_xc(sys[s], rounds, q.xc);
+      rounds_xc(sys[s], split, q.xc);
       const long xm = std::max(q.xc[0], q.xc[1]);
       const int PBt = std::max(1, 128 / nmom);
       const long ngroups = (q.naux + PBt - 1) / PBt;
@@ -388,7 +399,7 @@ mgw_status sigma_moments_batched_mixed(mgw_handle* h, const mgw_options* o, int 
     // item tables
     P->stages.clear();
     Blob blob;
-    Walker build{h, P, sys, nsys, nmom, &blob};
+    Walker<EpiY> build{h, P, sys, nsys, nmom, &blob};
     MGW_TRY(build.run());
     if (P->dtab_bytes < blob.b.size()) {
       if (P->dtab) cudaFree(P->dtab);
@@ -413,9 +424,12 @@ mgw_status sigma_moments_batched_mixed(mgw_handle* h, const mgw_options* o, int 
       const bool prof = h->prof;
       h->stream = h->capture_stream;
       h->prof = false;
+      const long before = h->launches;
       const cudaError_t ce = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
-      Walker go{h, P, sys, nsys, nmom, nullptr};
+      Walker<EpiY> go{h, P, sys, nsys, nmom, nullptr};
       const mgw_status st = ce == cudaSuccess ? go.run() : MGW_ERR_CUDA;
+      P->graph_launches = h->launches - before;  // kernels in the graph, counted when it runs
+      h->launches = before;
       cudaGraph_t graph = nullptr;
       const cudaError_t ee = ce == cudaSuccess ? cudaStreamEndCapture(h->stream, &graph) : ce;
       h->stream = user;
@@ -433,14 +447,22 @@ mgw_status sigma_moments_batched_mixed(mgw_handle* h, const mgw_options* o, int 
       }
       P->key = key;
     } else {
-      Walker go{h, P, sys, nsys, nmom, nullptr};
+      Walker<EpiY> go{h, P, sys, nsys, nmom, nullptr};
       MGW_TRY(go.run());
       return tc::check_tc_status(h, P->dstatus, "mgw_sigma_moments_batched");
     }
   }
   MGW_CUDA(h, cudaGraphLaunch(P->exec, h->stream));
-  h->launches += (long)P->stages.size();
+  h->launches += P->graph_launches;
   return tc::check_tc_status(h, P->dstatus, "mgw_sigma_moments_batched");
+}
+
+}  // namespace
+
+mgw_status sigma_moments_batched_mixed(mgw_handle* h, const mgw_options* o, int nsys, int nmom,
+                                       const mgw_system* sys) {
+  return nmom <= 12 ? batched_mixed<EpiBinomialTC<12>>(h, o, nsys, nmom, sys)
+                    : batched_mixed<EpiBinomialTC<kBinomMax>>(h, o, nsys, nmom, sys);
 }
 
 }  // namespace mgw
