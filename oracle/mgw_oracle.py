@@ -139,7 +139,19 @@ def quadrature_rule(nq: int, dmin: float, dmax: float):
     return z, w
 
 
-def rpa_eta0(Lov: np.ndarray, D: np.ndarray, nq: int) -> np.ndarray:
+def rpa_g_offset_exact(Lov: np.ndarray, D: np.ndarray) -> np.ndarray:
+    """G_offset of Eq. 25 with its z integral done in closed form.  Element
+    (P, ia) of the integrand is sum_jb (V D)_{P,jb} e^{-z D_jb} (V^T V)_{jb,ia}
+    e^{-z D_ia}, and int_0^inf e^{-z (D_jb + D_ia)} dz = 1 / (D_jb + D_ia)
+    (every D > 0), so
+      G_offset = V D + 4 (V D) [(V^T V) o C],  C_{jb,ia} = 1 / (D_jb + D_ia)
+    (a Cauchy matrix scaling V^T V elementwise)."""
+    VD = Lov * D[None, :]
+    C = 1.0 / (D[:, None] + D[None, :])
+    return VD + 4.0 * VD @ ((Lov.T @ Lov) * C)
+
+
+def rpa_eta0(Lov: np.ndarray, D: np.ndarray, nq: int, offset: str = "quadrature") -> np.ndarray:
     """RPA zeroth moment, Sec. II B, Eqs. 23-28.
 
     G = G_main + G_offset with
@@ -147,9 +159,12 @@ def rpa_eta0(Lov: np.ndarray, D: np.ndarray, nq: int) -> np.ndarray:
       G_offset = V D + 4 int_0^inf V D E(z) V^T V E(z) dz
       Q(z) = 4 V F(z) D V^T,  F(z) = (D^2 + z^2)^-1,  E(z) = exp(-z D),
     the G_main integrand being even in z (so 1/pi over R = 2/pi over
-    [0, inf)), both by the rule of quadrature_rule; then
+    [0, inf)), both by the rule of quadrature_rule (offset="exact": G_offset
+    by rpa_g_offset_exact instead); then
       eta~(0) = G D^-1 (I - 4 V^T (I + 4 V D^-1 V^T)^-1 V D^-1).
     """
+    if offset not in ("quadrature", "exact"):
+        raise ValueError(offset)
     naux = Lov.shape[0]
     eye = np.eye(naux)
     z, w = quadrature_rule(nq, float(D.min()), float(D.max()))
@@ -159,21 +174,25 @@ def rpa_eta0(Lov: np.ndarray, D: np.ndarray, nq: int) -> np.ndarray:
         F = 1.0 / (D * D + zj * zj)
         Q = 4.0 * (Lov * (F * D)[None, :]) @ Lov.T
         G_main += (2.0 / math.pi) * wj * zj * zj * ((Q @ (np.linalg.inv(eye + Q) - eye)) @ (Lov * F[None, :]))
-        E = np.exp(-zj * D)
-        G_off += 4.0 * wj * (((Lov * (D * E)[None, :]) @ Lov.T) @ (Lov * E[None, :]))
+        if offset == "quadrature":
+            E = np.exp(-zj * D)
+            G_off += 4.0 * wj * (((Lov * (D * E)[None, :]) @ Lov.T) @ (Lov * E[None, :]))
+    if offset == "exact":
+        G_off = rpa_g_offset_exact(Lov, D)
     G = G_main + G_off
     GDi = G / D[None, :]
     S = eye + 4.0 * (Lov / D[None, :]) @ Lov.T
     return GDi - 4.0 * (GDi @ Lov.T) @ np.linalg.solve(S, Lov / D[None, :])
 
 
-def rpa_response_moments(Lov: np.ndarray, D: np.ndarray, nmom: int, nq: int) -> np.ndarray:
+def rpa_response_moments(Lov: np.ndarray, D: np.ndarray, nmom: int, nq: int,
+                         offset: str = "quadrature") -> np.ndarray:
     """RPA screening, Sec. II B: eta~(0) from Eq. 23, eta~(1) = V D (Eq. 29),
     eta~(n) = eta~(n-2) (D^2 + 4 V^T V D) (Eq. 30), applied as
     eta~ D^2 + 4 (eta~ V^T)(V D).  Returns W(n) = eta~(n) V^T."""
     naux = Lov.shape[0]
     W = np.empty((nmom, naux, naux))
-    T = [rpa_eta0(Lov, D, nq), Lov * D[None, :]]
+    T = [rpa_eta0(Lov, D, nq, offset), Lov * D[None, :]]
     LD = Lov * D[None, :]
     for n in range(nmom):
         if n >= 2:
@@ -182,11 +201,11 @@ def rpa_response_moments(Lov: np.ndarray, D: np.ndarray, nmom: int, nq: int) -> 
     return W
 
 
-def response_moments(Lov, D, nmom, screening="tda", nq=48):
+def response_moments(Lov, D, nmom, screening="tda", nq=48, offset="quadrature"):
     if screening == "tda":
         return tda_response_moments(Lov, D, nmom)
     if screening == "rpa":
-        return rpa_response_moments(Lov, D, nmom, nq)
+        return rpa_response_moments(Lov, D, nmom, nq, offset)
     raise ValueError(screening)
 
 

@@ -55,6 +55,15 @@ def sigma_pin_error(mod, screening="tda"):
     return max(max(rel(sh[n], bh[n]), rel(sp[n], bp[n])) for n in range(nmom))
 
 
+def offset_pin_error(mod):
+    """eta~(0) with the exact G_offset against the brute-force A/B solution."""
+    eps, L = system(nocc=3, nvir=6, naux=14, scale=3.0)
+    D = mod.energy_differences(eps, 3)
+    Lov = mod.particle_hole_block(L, 3)
+    eta0, _, _, V = brute.rpa_eta_bruteforce(eps, L, 3, 0)
+    return rel(mod.rpa_eta0(Lov, D, 48, "exact"), V @ eta0)
+
+
 def lanczos_pin_error(mod):
     eps, L = system(nocc=3, nvir=6, naux=14)
     nmom = 8
@@ -168,6 +177,10 @@ CASES = [
     (["rpa_eta0"], "G_off += 4.0 * wj", "G_off += 2.0 * wj", "sigma", "rpa"),
     (["rpa_eta0"], "(np.linalg.inv(eye + Q) - eye)", "(np.linalg.inv(eye + Q) + eye)", "sigma", "rpa"),
     (["rpa_eta0"], "S = eye + 4.0 *", "S = eye - 4.0 *", "sigma", "rpa"),
+    (["rpa_g_offset_exact"], "C = 1.0 / (D[:, None] + D[None, :])", "C = 0.5 / np.sqrt(D[:, None] * D[None, :])",
+     "offset", None),
+    (["rpa_g_offset_exact"], "return VD + 4.0 * VD @", "return VD + 2.0 * VD @", "offset", None),
+    (["rpa_g_offset_exact"], "((Lov.T @ Lov) * C)", "((Lov.T @ Lov) @ C)", "offset", None),
     (["sigma_moments"], "sign = -1.0 if hole else 1.0", "sign = 1.0", "sigma", "tda"),
     (["sigma_moments"], "wgt = 2.0 *", "wgt = 1.0 *", "sigma", "tda"),
     # the W^(n) index printed inside the t-sum of Eqs. 6-7
@@ -219,6 +232,8 @@ def test_pins_catch_planted_mistake(case):
         err = qsgw_pin_error(mod)
     elif pin == "scgw":
         err = scgw_pin_error(mod)
+    elif pin == "offset":
+        err = offset_pin_error(mod)
     else:
         err = qp_pin_error(mod)
     assert not (err < 1e-6), f"planted mistake went unnoticed: {old!r} -> {new!r} (err {err})"
@@ -234,4 +249,5 @@ def test_unmutated_copy_passes_every_pin():
     assert naf_pin_error(mod) < 1e-10
     assert qsgw_pin_error(mod) < 1e-6
     assert scgw_pin_error(mod) < 1e-6
+    assert offset_pin_error(mod) < 1e-10
     assert math.isfinite(lanczos_pin_error(orc))

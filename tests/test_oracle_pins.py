@@ -91,6 +91,45 @@ def test_rpa_eta0_quadrature_converges_to_exact():
     assert errs[0] > errs[1] > errs[2]  # exponential decay with the node count
 
 
+def test_rpa_g_offset_exact_equals_the_integral():
+    """The closed-form G_offset (Cauchy matrix) against Eq. 25's integral taken
+    numerically element by element with adaptive quadrature (scipy), a route
+    independent of both the closed form and the Clenshaw-Curtis rule."""
+    integrate = pytest.importorskip("scipy.integrate")
+    eps, L = small_system(nocc=2, nvir=3, naux=4, scale=3.0)
+    D = orc.energy_differences(eps, 2)
+    V = orc.particle_hole_block(L, 2)
+    VD, M = V * D[None, :], V.T @ V
+    got = orc.rpa_g_offset_exact(V, D)
+    for P in range(V.shape[0]):
+        for ia in range(D.size):
+            f = lambda z: 4.0 * np.sum(VD[P] * np.exp(-z * D) * M[:, ia]) * math.exp(-z * D[ia])
+            val, _ = integrate.quad(f, 0.0, np.inf, epsabs=1e-15, epsrel=1e-13, limit=200)
+            assert abs(got[P, ia] - (VD[P, ia] + val)) < 1e-12 * max(1.0, abs(got[P, ia]))
+
+
+def test_rpa_eta0_exact_offset_matches_bruteforce():
+    """eta~(0) with the exact G_offset (only G_main by quadrature) against the
+    brute-force A/B diagonalisation; and the quadrature G_offset converges to
+    the exact one with the node count."""
+    eps, L = small_system(nocc=4, nvir=9, naux=20, scale=3.0)
+    nocc = 4
+    D = orc.energy_differences(eps, nocc)
+    Lov = orc.particle_hole_block(L, nocc)
+    eta0, _, _, V = brute.rpa_eta_bruteforce(eps, L, nocc, 0)
+    assert rel(orc.rpa_eta0(Lov, D, 48, "exact"), V @ eta0) < 1e-12
+    exact = orc.rpa_g_offset_exact(Lov, D)
+    errs = []
+    for nq in (8, 16, 32):
+        z, w = orc.quadrature_rule(nq, float(D.min()), float(D.max()))
+        G = Lov * D[None, :]
+        for zj, wj in zip(z, w):
+            E = np.exp(-zj * D)
+            G = G + 4.0 * wj * (((Lov * (D * E)[None, :]) @ Lov.T) @ (Lov * E[None, :]))
+        errs.append(rel(G, exact))
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-9
+
+
 def test_rpa_eta0_one_pair_closed_form():
     # nocc = nvir = naux = 1: eta(0) = d / Omega, Omega = sqrt(d (d + 4 v^2))
     eps = np.array([-0.7, 0.9])
@@ -100,6 +139,8 @@ def test_rpa_eta0_one_pair_closed_form():
     d = D[0]
     Om = math.sqrt(d * (d + 4 * v * v))
     t0 = orc.rpa_eta0(orc.particle_hole_block(L, 1), D, 48)
+    assert abs(t0[0, 0] - v * d / Om) < 1e-13
+    t0 = orc.rpa_eta0(orc.particle_hole_block(L, 1), D, 48, "exact")
     assert abs(t0[0, 0] - v * d / Om) < 1e-13
 
 
