@@ -85,6 +85,10 @@ typedef struct {
                         replay it while the problem table is unchanged; default 1 */
   int batch_autotune;/* mgw_sigma_moments_batched: time the candidate tile shapes of each grouped
                         stage on the first call for a problem table and keep the fastest; default 1 */
+  int rpa_offset;    /* G_offset of the RPA eta~(0) (Eq. 25): 0 by the quadrature nodes of Eq. 24;
+                        1 in closed form, V D + 4 (V D)[(V^T V) o C] with C_jb,ia = 1/(D_jb + D_ia),
+                        in column blocks of V^T V (4 ov^2 naux flops against the quadrature's
+                        4 nquad naux^2 ov: cheaper where ov < nquad naux); default 0 */
 } mgw_options;
 
 /* Fill *o with the defaults listed above. */

@@ -181,6 +181,7 @@ void mgw_options_default(mgw_options* o) {
   o->diis_space = 12;
   o->batch_graph = 1;
   o->batch_autotune = 1;
+  o->rpa_offset = 0;
 }
 
 mgw_status mgw_create(mgw_handle** out, int device, void* stream) {

@@ -147,9 +147,79 @@ __global__ void k_recip_sq(long n, const double* D, double* r, double* d2) {
   if (i < n) { r[i] = 1.0 / D[i]; d2[i] = D[i] * D[i]; }
 }
 
+// Vt [ov][naux] = V [naux][ov]^T through a 32 x 32 shared-memory tile
+__global__ void k_transpose(int naux, long ov, const double* __restrict__ V, double* __restrict__ Vt) {
+  __shared__ double t[32][33];
+  const long c0 = (long)blockIdx.x * 32, r0 = (long)blockIdx.y * 32;
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const long r = r0 + j, c = c0 + threadIdx.x;
+    t[j][threadIdx.x] = (r < naux && c < ov) ? V[r * ov + c] : 0.0;
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const long c = c0 + j, r = r0 + threadIdx.x;
+    if (c < ov && r < naux) Vt[c * naux + r] = t[threadIdx.x][j];
+  }
+}
+
+// S [ov][bw] /= D[jb] + D[i0 + i]: the Cauchy factor of the exact G_offset
+__global__ void k_cauchy_scale(long ov, int bw, long i0, const double* __restrict__ D, double* S) {
+  const long n = ov * bw;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < n; idx += (long)gridDim.x * blockDim.x) {
+    const long jb = idx / bw, i = idx % bw;
+    S[idx] /= D[jb] + D[i0 + i];
+  }
+}
+// G [naux][ov] columns i0.. += alpha X [naux][bw]
+__global__ void k_add_block(int naux, long ov, int bw, long i0, double alpha, const double* __restrict__ X,
+                            double* G) {
+  const long n = (long)naux * bw;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < n; idx += (long)gridDim.x * blockDim.x) {
+    const long p = idx / bw, i = idx % bw;
+    G[p * ov + i0 + i] += alpha * X[idx];
+  }
+}
+
+// G += 4 (V D)[(V^T V) o C], C_jb,ia = 1/(D_jb + D_ia): the z integral of
+// Eq. 25 in closed form (int_0^inf e^{-z (D_jb + D_ia)} dz).  V^T V is
+// formed and scaled one block of bw columns ia at a time (ov x bw), then
+// multiplied by V D (in VD) into those columns of G: 4 ov^2 naux flops and
+// ov bw doubles of scratch.  On the tensor cores both products are the
+// FP64-accurate digit-sliced GEMM (V^T is formed once for the first).
+static mgw_status g_offset_exact(mgw_handle* h, const RpaProducts& P, int naux, long ov, const double* V,
+                                 const double* D, const double* VD, double* G) {
+  const int bw = (int)std::min<long>(ov, 2048);
+  double *S = nullptr, *X = nullptr, *Vt = nullptr;
+  MGW_TRY(slot_buffer(h, 88, (size_t)ov * bw, &S));
+  if (P.tc) {
+    MGW_TRY(slot_buffer(h, 89, (size_t)naux * bw, &X));
+    MGW_TRY(slot_buffer(h, 90, (size_t)ov * naux, &Vt));
+    k_transpose<<<dim3((unsigned)((ov + 31) / 32), (unsigned)((naux + 31) / 32)), dim3(32, 8), 0, h->stream>>>(
+        naux, ov, V, Vt);
+    MGW_TRY(check_launch(h, "transpose"));
+  }
+  const unsigned gs = (unsigned)std::min<long>(((long)ov * bw + 255) / 256, 152L * 16);
+  for (long i0 = 0; i0 < ov; i0 += bw) {
+    const int nb = (int)std::min<long>(bw, ov - i0);
+    if (P.tc) MGW_TRY(oz::gemm_fp64_tc_nn(h, (int)ov, nb, naux, Vt, naux, V + i0, ov, S, nb, "rpa_offset_vtv"));
+    else MGW_TRY(gemm_tn(h, ov, nb, naux, 1.0, V, ov, V + i0, ov, 0.0, S, nb));
+    k_cauchy_scale<<<gs, 256, 0, h->stream>>>(ov, nb, i0, D, S);
+    MGW_TRY(check_launch(h, "cauchy_scale"));
+    if (P.tc) {
+      MGW_TRY(oz::gemm_fp64_tc_nn(h, naux, nb, (int)ov, VD, ov, S, nb, X, nb, "rpa_offset_g"));
+      const unsigned ga = (unsigned)std::min<long>(((long)naux * nb + 255) / 256, 152L * 16);
+      k_add_block<<<ga, 256, 0, h->stream>>>(naux, ov, nb, i0, 4.0, X, G);
+      MGW_TRY(check_launch(h, "add_block"));
+    } else {
+      MGW_TRY(gemm_nn(h, naux, nb, ov, 4.0, VD, ov, S, nb, 1.0, G + i0, ov));
+    }
+  }
+  return MGW_OK;
+}
+
 // eta~(0) of the RPA, Eqs. 23-28 (see the quadrature note above).
-static mgw_status rpa_eta0(mgw_handle* h, const RpaProducts& P, int naux, long ov, int nq, const double* V,
-                           const double* D, double dmin, double dmax, double* T0, double* work) {
+static mgw_status rpa_eta0(mgw_handle* h, const RpaProducts& P, int naux, long ov, int nq, bool exact_offset,
+                           const double* V, const double* D, double dmin, double dmax, double* T0, double* work) {
   // work layout: G[naux*ov] B1[naux*ov] Q[naux^2] X[naux^2] IQ[naux^2] fac[4*ov]
   const long na2 = (long)naux * naux;
   double* G = work;
@@ -166,8 +236,12 @@ static mgw_status rpa_eta0(mgw_handle* h, const RpaProducts& P, int naux, long o
   quadrature(nq, dmin, dmax, z, w);
   const unsigned gov = (unsigned)((ov + 255) / 256);
 
-  // G_offset starts at V D
+  // G_offset starts at V D; in closed form it is completed here, else node by node below
   MGW_TRY(scale_columns(h, naux, ov, V, D, G));
+  if (exact_offset) {
+    MGW_TRY(scale_columns(h, naux, ov, V, D, B1));
+    MGW_TRY(g_offset_exact(h, P, naux, ov, V, D, B1, G));
+  }
   for (int j = 0; j < nq; ++j) {
     k_node_factors<<<gov, 256, 0, h->stream>>>(ov, D, z[j], fFD, fF, fDE, fE);
     MGW_TRY(check_launch(h, "node_factors"));
@@ -186,6 +260,7 @@ static mgw_status rpa_eta0(mgw_handle* h, const RpaProducts& P, int naux, long o
     MGW_TRY(scale_columns(h, naux, ov, V, fF, B1));
     MGW_TRY(P.nn((2.0 / pi) * w[j] * z[j] * z[j], X, B1, 1.0, G));
     // G += 4 w (V D E V^T)(V E)   (Eq. 25)
+    if (exact_offset) continue;
     MGW_TRY(scale_columns(h, naux, ov, V, fDE, B1));
     MGW_TRY(P.nt(1.0, B1, 0.0, Q));
     MGW_TRY(scale_columns(h, naux, ov, V, fE, B1));
@@ -394,7 +469,7 @@ static mgw_status response_impl(mgw_handle* h, const mgw_options* o, int nocc, i
     MGW_TRY(oz::slice_rows(h, naux, ov, Lov, ov, P.sv));
     MGW_TRY(oz::digit_map(h, &P.mv, P.sv, oz::BN));
   }
-  MGW_TRY(rpa_eta0(h, P, naux, ov, o->nquad, Lov, D, hmm[0], hmm[1], T0, work));
+  MGW_TRY(rpa_eta0(h, P, naux, ov, o->nquad, o->rpa_offset != 0, Lov, D, hmm[0], hmm[1], T0, work));
   MGW_CUDA(h, cudaMemcpyAsync(T1, LD, sizeof(double) * tsz, cudaMemcpyDeviceToDevice, h->stream));
   double* T[2] = {T0, T1};
   for (int n = 0; n < nmom; ++n) {

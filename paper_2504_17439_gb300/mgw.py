@@ -42,6 +42,7 @@ class Options(ctypes.Structure):
         ("diis_space", ctypes.c_int),
         ("batch_graph", ctypes.c_int),
         ("batch_autotune", ctypes.c_int),
+        ("rpa_offset", ctypes.c_int),
     ]
 
 

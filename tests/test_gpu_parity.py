@@ -81,6 +81,25 @@ def test_response_moments(h, shape, screening, precision):
         assert rel(got[n], ref[n]) < TOL, (n, rel(got[n], ref[n]))
 
 
+@pytest.mark.parametrize("nocc,nvir,naux", [(3, 8, 20), (12, 200, 150)])
+@pytest.mark.parametrize("precision", ["fp64", "fp64_tc"])
+def test_rpa_response_with_exact_offset(h, nocc, nvir, naux, precision):
+    """RPA response moments with G_offset in closed form (rpa_offset = 1)
+    against the oracle's closed form; ov = 2400 spans two column blocks of
+    V^T V (2048 wide) with a ragged second one."""
+    from paper_2504_17439_gb300 import mgw
+
+    eps, L = system(nocc, nvir, naux, 41, scale=2.0)
+    nmom = 6
+    D = orc.energy_differences(eps, nocc)
+    Lov = orc.particle_hole_block(L, nocc)
+    ref = orc.response_moments(Lov, D, nmom, "rpa", 48, "exact")
+    o = mgw.options(screening=mgw.MGW_RPA, precision=precision_of(precision), rpa_offset=1)
+    got = host(h.mgw_response_moments(o, nocc, nvir, naux, nmom, dev(eps), dev(Lov)))
+    for n in range(nmom):
+        assert rel(got[n], ref[n]) < TOL, (n, rel(got[n], ref[n]))
+
+
 @pytest.mark.parametrize("shape", SHAPES)
 def test_extract_ov(h, shape):
     nocc, nvir, naux, N, seed = shape
